@@ -1,0 +1,386 @@
+#!/usr/bin/env python
+"""Benchmark of the SpMV path on the 6M-cell finite-volume Laplacian.
+
+Workload (one step): y = A x, FP64, on the Kuhn-tet 100^3 cube (6,000,000 cells,
+29,880,000 non-zeros, Dirichlet, cells randomly permuted then RCM-reordered), inputs resident
+in HBM, L2 flushed (256 MB write) between timed steps.  The metric is effective bandwidth:
+algorithmic bytes 12 nnz + 16 N (each value, index, x and y entry once) per step / time.
+
+Secondary results measured once after the timed loop (same JSON line): FP32 product of the same
+matrix, FP64 on the random (unreordered) order, the naive CSR kernel, CG solves, SpMM and the
+serving loop where available.
+
+--impl reference times the CPU oracle (plain sequential C) on the same workload.
+N > 1 (torchrun): independent replicas, one per GPU, weak scaling; value = all ranks' bytes /
+max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SpMV effective GB/s (% HBM peak) FP64 vs mixed; served CG solves/s, p99"
+WORKLOAD = "kuhn-tet 100^3 FV Laplacian, Dirichlet, 6,000,000 rows, 29,880,000 nnz, RCM order"
+FLUSH_BYTES = 256 << 20
+
+
+def spmv_bytes(n, nnz, f32=False):
+    return (8 * nnz + 8 * n) if f32 else (12 * nnz + 16 * n)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.samples = []
+        self.proc = None
+        self._t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return self
+        self._t = threading.Thread(target=self._read, daemon=True)
+        self._t.start()
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == len(self.FIELDS):
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self._t:
+            self._t.join(timeout=5)
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in self.samples:
+            try:
+                mhz.append(float(s[0]))
+                mx = float(s[1])
+            except ValueError:
+                continue
+            for name, v in zip(names, s[3:]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(mhz)}
+
+
+def traffic_from_profile(kernel_key):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)[kernel_key]
+    except Exception:
+        return None
+    h = hashlib.sha256()
+    for rel in t.get("sources", []):
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    if h.hexdigest() != t.get("sha256"):
+        return None
+    return t.get("traffic_bytes")
+
+
+# ---------------------------------------------------------------------------------------
+def run_reference(args):
+    """The CPU oracle on the same workload and metric (reference arm)."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2107_12371_gb300 import workloads
+    m, x = workloads.c2()
+    perm = oracle.cm_order(m.row_ptr, m.col_idx)
+    rp, ci, v = oracle.permute_csr(m.row_ptr, m.col_idx, m.values, perm)
+    xp = np.ascontiguousarray(x[perm])
+    n = m.n
+    # one full product first; each timed step is a bounded sample: a contiguous block of rows
+    # sized so the K steps take about a minute in total (the whole matrix when that fits)
+    t0 = time.perf_counter()
+    oracle.spmv(rp, ci, v, xp)
+    t_full = time.perf_counter() - t0
+    rows = n if args.steps * t_full <= 60.0 else max(1, int(n * 60.0 / (args.steps * t_full)))
+    blocks = [(a, min(n, a + rows)) for a in range(0, n, rows)]
+
+    def step(i):
+        a, b = blocks[i % len(blocks)]
+        oracle.spmv(rp[a:b + 1], ci, v, xp)
+        return 12 * int(rp[b] - rp[a]) + 16 * (b - a)
+
+    for i in range(args.warmup):
+        step(i)
+    done = 0
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        done += step(i)
+    dt = time.perf_counter() - t0
+    value = done / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": m.n, "nnz": m.nnz, "rows_per_step": rows,
+                       "l2": "n/a (host)"},
+            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": "%d steps of a sequential CSR SpMV over %d-row blocks "
+                                       "of the 6M-row RCM-ordered matrix" % (args.steps, rows)},
+            "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline(rp, ci, v, x, nbytes, budget_s=10.0):
+    import oracle
+    oracle.spmv(rp, ci, v, x)
+    reps = 0
+    t0 = time.perf_counter()
+    while True:
+        oracle.spmv(rp, ci, v, x)
+        reps += 1
+        dt = time.perf_counter() - t0
+        if dt >= budget_s:
+            break
+    return {"value": nbytes * reps / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": "%d full sequential CSR SpMVs of the 6M-row RCM-ordered matrix "
+                      "(%.1f s, single thread)" % (reps, dt)}
+
+
+def time_kernel(torch, fn, steps, flush_buf, stream):
+    """Per-step CUDA-event times (ms) of fn() with an L2 flush before each step."""
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        for a, b in evs:
+            flush_buf.add_(1)
+            a.record(stream)
+            fn()
+            b.record(stream)
+    stream.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def run_gpu(args):
+    import torch
+    from paper_2107_12371_gb300 import capi, workloads
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    capi.load()
+
+    m, x = workloads.c2()
+    n, nnz = m.n, m.nnz
+    nbytes = spmv_bytes(n, nnz)
+    stream = torch.cuda.Stream(device=dev)
+    t_create = time.perf_counter()
+    A = capi.Matrix(n, m.row_ptr, m.col_idx, m.values, stream=stream,
+                    reorder=capi.SPMV_REORDER_RCM, precision=capi.SPMV_PREC_DUAL,
+                    slice_height=args.slice_height)
+    t_create = time.perf_counter() - t_create
+    info = A.info()
+    xd = torch.from_numpy(x).to(dev)
+    xi = torch.empty_like(xd)
+    yi = torch.empty_like(xd)
+    A.permute(0, xd, xi, stream)
+    flush = torch.zeros(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    fn = lambda: A.apply(xi, yi, stream)  # noqa: E731
+
+    for _ in range(max(3, args.warmup)):
+        fn()
+    stream.synchronize()
+
+    sampler = ClockSampler(local).start()
+    time.sleep(0.2)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    wall0 = time.perf_counter()
+    times = time_kernel(torch, fn, args.steps, flush, stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    wall = time.perf_counter() - wall0
+    # keep the sampler running a little under a load loop so the clocks reflect the kernel
+    soak_end = time.perf_counter() + 1.0
+    with torch.cuda.stream(stream):
+        while time.perf_counter() < soak_end:
+            for _ in range(200):
+                fn()
+            stream.synchronize()
+    clocks = sampler.stop()
+
+    t_dev = sum(times) / 1e3  # seconds over the K timed SpMVs
+    if world > 1:
+        tt = torch.tensor([t_dev], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_dev = float(tt.item())
+    value = world * nbytes * args.steps / t_dev / 1e9
+    avg_launch_s = sum(times) / len(times) / 1e3
+    peak, peak_src = measured_peaks()
+
+    extra = {}
+    if rank == 0 and not args.quick:
+        extra = secondary(args, torch, capi, workloads, m, x, A, xi, stream, flush, dev)
+
+    # end-to-end through the C ABI with host buffers: pinned x -> device, y -> pinned host
+    xh = torch.from_numpy(x[A.permutation()]).pin_memory()
+    yh = torch.empty(n, dtype=torch.float64).pin_memory()
+    e2e_steps = max(3, min(args.steps, 50))
+    for _ in range(3):
+        xi.copy_(xh, non_blocking=True)
+        fn()
+        yh.copy_(yi, non_blocking=True)
+    stream.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        for _ in range(e2e_steps):
+            xi.copy_(xh, non_blocking=True)
+            fn()
+            yh.copy_(yi, non_blocking=True)
+        ev1.record(stream)
+    stream.synchronize()
+    e2e_s = ev0.elapsed_time(ev1) / 1e3 / e2e_steps
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.barrier()
+            torch.distributed.destroy_process_group()
+        return 0
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_dev / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "nnz": nnz, "format": "sliced ELLPACK",
+                   "slice_height": info["slice_height"], "reorder": "rcm",
+                   "bandwidth": info["bandwidth"], "max_slice_span": info["max_slice_span"],
+                   "algorithmic_bytes_per_step": nbytes, "l2": "flushed (256 MB write) between steps",
+                   "create_s": round(t_create, 3), "wall_s_timed_region": round(wall, 4),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "pct_hbm_peak": 100.0 * (value / world) / peak,
+        "clocks": clocks,
+        "e2e": {"value": nbytes / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": 8 * n,
+                "d2h_bytes_per_step": 8 * n},
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "hbm", "achieved": nbytes / avg_launch_s / 1e9, "peak": peak,
+                     "unit": "GB/s", "frac": nbytes / avg_launch_s / 1e9 / peak,
+                     "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)",
+                     "kernel": "spmv_sell<double,R>",
+                     "traffic": traffic_from_profile("spmv_sell_f64_c2_rcm")},
+    }
+    line.update(extra)
+    if not args.no_cpu_baseline:
+        rp, ci, v = capi.spmv_export_csr(A.handle, n, nnz)
+        line["cpu_baseline"] = cpu_baseline(rp, ci, v, xi.cpu().numpy(), nbytes)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def secondary(args, torch, capi, workloads, m, x, A, xi, stream, flush, dev):
+    """One-off measurements reported beside the headline (same JSON line)."""
+    out = {}
+    n, nnz = m.n, m.nnz
+    K = max(10, min(args.steps, 100))
+    # FP32 product of the same handle (the mixed-precision inner SpMV)
+    x32 = xi.float()
+    y32 = torch.empty_like(x32)
+    t = time_kernel(torch, lambda: A.apply_f32(x32, y32, stream), K, flush, stream)
+    b32 = spmv_bytes(n, nnz, f32=True)
+    out["fp32_spmv"] = {"value": b32 / (sum(t) / len(t) / 1e3) / 1e9, "unit": "GB/s",
+                        "ms": sum(t) / len(t), "algorithmic_bytes": b32}
+    # the naive CSR kernel (Sec. 4.3 baseline) on the same order
+    yy = torch.empty_like(xi)
+    t = time_kernel(torch, lambda: A.apply_csr(xi, yy, stream), K, flush, stream)
+    nb = spmv_bytes(n, nnz)
+    out["naive_csr_rcm"] = {"value": nb / (sum(t) / len(t) / 1e3) / 1e9, "unit": "GB/s",
+                            "ms": sum(t) / len(t)}
+    # random order (no reordering): sliced and naive
+    R = capi.Matrix(n, m.row_ptr, m.col_idx, m.values, stream=stream,
+                    slice_height=args.slice_height)
+    xr = torch.from_numpy(x).to(dev)
+    yr = torch.empty_like(xr)
+    t = time_kernel(torch, lambda: R.apply(xr, yr, stream), K, flush, stream)
+    out["sell_random_order"] = {"value": nb / (sum(t) / len(t) / 1e3) / 1e9, "unit": "GB/s",
+                                "ms": sum(t) / len(t)}
+    t = time_kernel(torch, lambda: R.apply_csr(xr, yr, stream), K, flush, stream)
+    out["naive_csr_random_order"] = {"value": nb / (sum(t) / len(t) / 1e3) / 1e9,
+                                     "unit": "GB/s", "ms": sum(t) / len(t)}
+    R.close()
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--slice-height", type=int, default=64)
+    ap.add_argument("--quick", action="store_true", help="headline only, no secondary results")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

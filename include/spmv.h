@@ -1,0 +1,230 @@
+/*
+ * spmv.h -- C ABI of the GB300 sparse matrix-vector library for finite-volume CFD matrices.
+ *
+ * What it computes (the paper's hot path and what is grown around it):
+ *   y = A x for a square sparse matrix A from an unstructured finite-volume mesh, where the
+ *   sparsity pattern drives indirect gathers of x (Sec. 2; Sec. 4.3 "naive implementation").
+ *   Pre-processing, applied once per matrix: optional (reverse) Cuthill-McKee reordering
+ *   (Sec. 4.1), conversion to sliced ELLPACK with S rows per slice stored column-major inside
+ *   a slice (Sec. 4.2), and the per-slice first/last column of x that the slice reads
+ *   (Sec. 5.1, col_start / col_end).  Around the SpMV: multi-right-hand-side products,
+ *   Jacobi-preconditioned CG in FP64, CG with FP32 inner solves and FP64 iterative
+ *   refinement, and a continuous-batching solve server (none of these are in the paper).
+ *
+ * Conventions for every entry point:
+ *   - Every call returns an spmv_status_t and never aborts the process.
+ *   - "Device pointer" means memory of the current CUDA device; "host pointer" means
+ *     ordinary (optionally pinned) host memory.
+ *   - stream is a cudaStream_t passed as void* (NULL = the legacy default stream).  Calls
+ *     marked "async" only enqueue work on that stream; calls marked "sync" return after the
+ *     work is complete.
+ *   - Vectors of a reordered matrix live in the reordered ("internal") numbering; convert
+ *     with spmv_permute.
+ *   - Index type int32 (row_ptr, col_idx), so nnz < 2^31.
+ */
+#ifndef GB300_SPMV_H
+#define GB300_SPMV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct spmv_matrix_s *spmv_matrix_t;
+typedef struct spmv_server_s *spmv_server_t;
+
+typedef enum {
+    SPMV_OK = 0,
+    SPMV_ERR_INVALID_ARG = 1,   /* null pointer, negative size, unsupported option value   */
+    SPMV_ERR_INVALID_CSR = 2,   /* row_ptr not monotone, column out of range, unsorted/dup  */
+    SPMV_ERR_OOM = 3,           /* a device allocation failed                               */
+    SPMV_ERR_BUDGET = 4,        /* a server request can never fit the memory budget        */
+    SPMV_ERR_CUDA = 5,          /* any other CUDA runtime error                             */
+    SPMV_ERR_NOT_CONVERGED = 6, /* CG reached its iteration cap                             */
+    SPMV_ERR_TIMEOUT = 7,       /* a bounded device-side wait or a solve deadline expired   */
+    SPMV_ERR_PENDING = 8,       /* server request not finished yet                          */
+    SPMV_ERR_UNSUPPORTED = 9    /* operation not available for this handle's precision     */
+} spmv_status_t;
+
+/* reorder */
+#define SPMV_REORDER_NONE 0
+#define SPMV_REORDER_RCM 1 /* reverse Cuthill-McKee (Sec. 4.1 uses CM; same bandwidth) */
+#define SPMV_REORDER_CM 2
+
+/* precision: which value arrays the handle stores */
+#define SPMV_PREC_FP64 0 /* FP64 values (12 bytes per non-zero with the int32 column)       */
+#define SPMV_PREC_FP32 1 /* FP32 values only (8 bytes per non-zero)                         */
+#define SPMV_PREC_DUAL 2 /* FP64 and FP32 values: FP64 and FP32 products, mixed-precision CG */
+
+/* variant of the SpMV kernel */
+#define SPMV_VARIANT_AUTO 0
+#define SPMV_VARIANT_CSR 1         /* thread per CSR row, x gathered from global memory (Sec. 4.3) */
+#define SPMV_VARIANT_SELL 2        /* sliced ELLPACK, A streamed, x kept resident in L2        */
+#define SPMV_VARIANT_SELL_WINDOW 3 /* sliced ELLPACK, x staged per CTA in a shared-memory window (Sec. 5.1) */
+
+typedef struct {
+    int slice_height;    /* S, rows per slice: 32, 64, 128 or 256 (0 = default 64)            */
+    int block;           /* threads per CTA for the SpMV kernels: 64..1024, multiple of 32 (0 = 256) */
+    int variant;         /* SPMV_VARIANT_*                                                   */
+    int reorder;         /* SPMV_REORDER_*                                                   */
+    int precision;       /* SPMV_PREC_*                                                      */
+    int autotune;        /* 1: time the candidate (S, block, variant) on this matrix and keep the fastest */
+    int peripheral;      /* 1: George-Liu pseudo-peripheral start node for (R)CM             */
+    int window_words;    /* SELL_WINDOW capacity in x entries per CTA (0 = largest that fits) */
+} spmv_options_t;
+
+/* Fills *opt with the defaults (S = 64, block = 256, AUTO variant, no reordering, FP64,
+ * no autotuning, peripheral start on).  Returns SPMV_ERR_INVALID_ARG if opt is NULL. */
+spmv_status_t spmv_default_options(spmv_options_t *opt);
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *spmv_status_string(spmv_status_t status);
+
+/*
+ * spmv_create -- sync.  Builds a matrix handle from CSR (Sec. 4.2 input; Sec. 4.1 reordering;
+ * Sec. 4.2 sliced ELLPACK; Sec. 5.1 per-slice column range).
+ *   n_rows == n_cols (square) >= 0; nnz >= 0; row_ptr int32[n_rows+1] with row_ptr[0] = 0 and
+ *   row_ptr[n_rows] = nnz; col_idx int32[nnz], strictly increasing inside each row, in
+ *   [0, n_cols); values double[nnz].
+ *   inputs_on_device: 0 = the three arrays are host pointers, 1 = device pointers.
+ *   The arrays are copied; the caller keeps ownership and may free them after return.
+ *   opt may be NULL (defaults).  On success *out owns every device buffer of the matrix.
+ * Errors: INVALID_ARG (null pointers, n_rows != n_cols, bad options), INVALID_CSR (the checks
+ * above, run on the device), OOM, CUDA.  On error *out is set to NULL.
+ */
+spmv_status_t spmv_create(int32_t n_rows, int32_t n_cols, int64_t nnz, const int32_t *row_ptr,
+                          const int32_t *col_idx, const double *values, int inputs_on_device,
+                          const spmv_options_t *opt, void *stream, spmv_matrix_t *out);
+
+/* Frees every device buffer of the handle (synchronizes the device first).  NULL is a no-op. */
+spmv_status_t spmv_destroy(spmv_matrix_t A);
+
+/* Sizes and choices of a handle.  Any output pointer may be NULL. */
+typedef struct {
+    int32_t n_rows;
+    int64_t nnz;
+    int32_t slice_height;    /* S actually used                                  */
+    int32_t block;           /* CTA size actually used                           */
+    int32_t variant;         /* kernel variant actually used                     */
+    int32_t precision;
+    int32_t reorder;
+    int32_t n_slices;
+    int64_t sell_entries;    /* stored sliced-ELLPACK entries, padding included   */
+    int32_t bandwidth;       /* max |row - col| in the internal numbering         */
+    int32_t max_slice_span;  /* max over slices of col_end - col_start            */
+    int32_t window_words;    /* shared-memory window capacity (SELL_WINDOW), else 0 */
+    size_t device_bytes;     /* device memory owned by the handle                 */
+} spmv_info_t;
+spmv_status_t spmv_get_info(spmv_matrix_t A, spmv_info_t *info);
+
+/* sync.  perm_host int32[n_rows]: perm[new] = old (identity when not reordered). */
+spmv_status_t spmv_get_permutation(spmv_matrix_t A, int32_t *perm_host);
+
+/* sync.  CSR of the matrix in the internal numbering (rows sorted by column), host arrays of
+ * n_rows+1, nnz and nnz entries.  values may be NULL for an FP32-only handle. */
+spmv_status_t spmv_export_csr(spmv_matrix_t A, int32_t *row_ptr, int32_t *col_idx, double *values);
+
+/* sync.  Sliced-ELLPACK arrays (Sec. 4.2) to host memory: slice_ptr int64[n_slices+1],
+ * col int32[sell_entries] (padding = -1), values double[sell_entries] (padding = 0.0; may be
+ * NULL), col_start / col_end int32[n_slices] (Sec. 5.1; may be NULL). */
+spmv_status_t spmv_export_sell(spmv_matrix_t A, int64_t *slice_ptr, int32_t *col, double *values,
+                               int32_t *col_start, int32_t *col_end);
+
+/*
+ * spmv_apply -- async.  y = A x (overwrites y) in the internal numbering (Sec. 4.3 / 5.2).
+ * x_dev, y_dev: device double[n_rows] (FP64 / DUAL handles); must not overlap.
+ * Summation order per row: ascending column, fused multiply-add from +0.0.
+ */
+spmv_status_t spmv_apply(spmv_matrix_t A, const double *x_dev, double *y_dev, void *stream);
+
+/* async.  y = A32 x with FP32 values, vector and accumulation (FP32 / DUAL handles). */
+spmv_status_t spmv_apply_f32(spmv_matrix_t A, const float *x_dev, float *y_dev, void *stream);
+
+/* async.  Naive CSR kernel (thread per row, x gathered from global memory; Sec. 4.3),
+ * kept as the baseline the sliced kernels are compared with.  FP64 / DUAL handles. */
+spmv_status_t spmv_apply_csr(spmv_matrix_t A, const double *x_dev, double *y_dev, void *stream);
+
+/*
+ * spmv_apply_multi -- async.  Y = A X for k right-hand sides, X and Y row-major
+ * (n_rows x k, entry (i, c) at i*k + c), device memory, FP64.  1 <= k <= 64.  Each gathered
+ * row of X is reused for all k columns.  Column c equals spmv_apply on column c bit for bit.
+ */
+spmv_status_t spmv_apply_multi(spmv_matrix_t A, int k, const double *X_dev, double *Y_dev,
+                               void *stream);
+/* async.  FP32 version of spmv_apply_multi (FP32 / DUAL handles). */
+spmv_status_t spmv_apply_multi_f32(spmv_matrix_t A, int k, const float *X_dev, float *Y_dev,
+                                   void *stream);
+
+/* async.  Converts a vector between the caller's numbering and the internal one:
+ * direction 0: out[new] = in[perm[new]]; direction 1: out[perm[new]] = in[new].
+ * elem_bytes 4 or 8; in/out device arrays of n_rows elements, must not overlap. */
+spmv_status_t spmv_permute(spmv_matrix_t A, int direction, int elem_bytes, const void *in_dev,
+                           void *out_dev, void *stream);
+
+/* ------------------------------ conjugate gradients ------------------------------------ */
+typedef struct {
+    double rtol;          /* stop when ||b - A x||_2 <= rtol ||b||_2 (default 1e-10)            */
+    int max_iter;         /* CG iteration cap (FP64) or cap per inner solve (mixed); default 20000 */
+    int mixed;            /* 0: FP64 Jacobi-PCG; 1: FP32 inner PCG + FP64 refinement (DUAL)   */
+    double inner_rtol;    /* mixed: relative residual reduction of each inner solve (1e-4)    */
+    int max_outer;        /* mixed: refinement steps cap (default 20)                          */
+    int use_x0;           /* 1: x_dev holds the starting guess; 0: start from x = 0            */
+    int persistent;       /* 1: one cooperative kernel per solve; 0: CUDA-graph batches of iterations */
+    int check_every;      /* graph path: iterations per graph launch between host checks (16) */
+    double timeout_s;     /* wall-clock limit of the solve, 0 = none                           */
+} cg_options_t;
+
+typedef struct {
+    int iterations;          /* CG iterations (mixed: inner iterations in total)        */
+    int outer_iterations;    /* mixed: refinement steps; FP64: recurrence restarts      */
+    double rel_residual;     /* ||b - A x||_2 / ||b||_2 recomputed in FP64 at the end   */
+    spmv_status_t status;
+} cg_result_t;
+
+spmv_status_t cg_default_options(cg_options_t *opt);
+
+/*
+ * cg_solve -- sync.  Solves A x = b for SPD A by Jacobi-preconditioned CG (FP64), or with
+ * opt->mixed by FP32 inner Jacobi-PCG and FP64 iterative refinement (residual, norms and the
+ * update of x in FP64).  b_dev, x_dev: device double[n_rows] in the internal numbering.
+ * Requires a non-zero diagonal entry in every row.  Returns NOT_CONVERGED / TIMEOUT with
+ * x_dev holding the last iterate; result (may be NULL) is filled in every case.
+ */
+spmv_status_t cg_solve(spmv_matrix_t A, const double *b_dev, double *x_dev, const cg_options_t *opt,
+                       cg_result_t *result, void *stream);
+
+/* ------------------------------ continuous-batching server ------------------------------ */
+typedef struct {
+    uint64_t submitted, completed, rejected;
+    int active_slots;        /* solves currently on the device                 */
+    int queued;              /* admitted to the queue, waiting for memory/slot */
+    size_t bytes_in_use;     /* device bytes held by active solves             */
+    size_t peak_bytes;
+    double p50_latency_s, p99_latency_s; /* over completed requests               */
+} spmv_server_stats_t;
+
+/* Creates a server with a device-memory budget (bytes) and at most max_slots solves in flight. */
+spmv_status_t spmv_server_create(size_t hbm_budget_bytes, int max_slots, spmv_server_t *out);
+
+/* Enqueues a solve of A x = b (host CSR + host b, copied before return).  opt->mixed selects
+ * the precision.  *ticket identifies the request.  BUDGET if it can never fit. */
+spmv_status_t spmv_server_submit(spmv_server_t s, int32_t n, int64_t nnz, const int32_t *row_ptr,
+                                 const int32_t *col_idx, const double *values, const double *b,
+                                 const cg_options_t *opt, uint64_t *ticket);
+
+/* PENDING until the request is done; then copies x (host double[n], original numbering) and
+ * the result, releases the request and returns its status. */
+spmv_status_t spmv_server_poll(spmv_server_t s, uint64_t ticket, double *x_host,
+                               cg_result_t *result);
+
+spmv_status_t spmv_server_get_stats(spmv_server_t s, spmv_server_stats_t *stats);
+
+/* Stops the worker, frees every request (finished or not) and the server. */
+spmv_status_t spmv_server_destroy(spmv_server_t s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GB300_SPMV_H */

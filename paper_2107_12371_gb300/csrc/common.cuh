@@ -1,0 +1,139 @@
+// common.cuh -- shared host/device definitions of the GB300 SpMV library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/spmv.h"
+
+namespace gb {
+
+// Number of SMs and other device facts, queried once per device.
+struct DeviceFacts {
+    int device = -1;
+    int sm_count = 0;
+    int max_smem_optin = 0;  // bytes of shared memory a CTA may opt into
+    int l2_bytes = 0;
+};
+const DeviceFacts &device_facts();
+
+// Status from a CUDA error code.
+inline spmv_status_t cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return SPMV_OK;
+    if (e == cudaErrorMemoryAllocation) return SPMV_ERR_OOM;
+    return SPMV_ERR_CUDA;
+}
+
+#define GB_CUDA(expr)                                            \
+    do {                                                         \
+        cudaError_t gb_e_ = (expr);                              \
+        if (gb_e_ != cudaSuccess) return ::gb::cuda_status(gb_e_); \
+    } while (0)
+
+#define GB_TRY(expr)                            \
+    do {                                        \
+        spmv_status_t gb_s_ = (expr);           \
+        if (gb_s_ != SPMV_OK) return gb_s_;     \
+    } while (0)
+
+#define GB_LAUNCHED() GB_CUDA(cudaGetLastError())
+
+// A device allocation owned by the handle.
+template <typename T>
+struct DevBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    spmv_status_t alloc(size_t count, size_t *tally) {
+        release(tally);
+        if (count == 0) count = 1;
+        cudaError_t e = cudaMalloc((void **)&p, count * sizeof(T));
+        if (e != cudaSuccess) {
+            p = nullptr;
+            cudaGetLastError();
+            return cuda_status(e);
+        }
+        n = count;
+        if (tally) *tally += count * sizeof(T);
+        return SPMV_OK;
+    }
+    void release(size_t *tally) {
+        if (p) {
+            cudaFree(p);
+            if (tally) *tally -= n * sizeof(T);
+        }
+        p = nullptr;
+        n = 0;
+    }
+};
+
+// Work vectors of a CG solve (allocated on first use, kept with the handle).
+struct CgWork {
+    DevBuf<double> r, z, p, q, dinv;
+    DevBuf<float> r32, p32, q32, d32, dinv32;
+    DevBuf<double> part;        // per-CTA partial sums
+    DevBuf<double> scal;        // device scalars
+    DevBuf<int> flags;          // status flags
+    int *h_flags = nullptr;     // pinned host mirror
+    double *h_scal = nullptr;   // pinned host mirror
+    int part_len = 0;
+    bool ready = false;
+};
+
+}  // namespace gb
+
+struct spmv_matrix_s {
+    int32_t n = 0;
+    int64_t nnz = 0;
+    spmv_options_t opt{};
+    int S = 64;        // rows per slice
+    int block = 256;   // threads per CTA
+    int variant = SPMV_VARIANT_SELL;
+    int window_words = 0;
+    int32_t bandwidth = 0;
+    int32_t max_span = 0;
+    int32_t n_slices = 0;
+    int64_t sell_entries = 0;
+    size_t bytes = 0;  // device bytes owned
+
+    gb::DevBuf<int32_t> perm;       // new -> old (only when reordered)
+    gb::DevBuf<int32_t> row_ptr;    // CSR, internal numbering
+    gb::DevBuf<int32_t> col;
+    gb::DevBuf<double> val;
+    gb::DevBuf<float> val32;
+    gb::DevBuf<int64_t> slice_ptr;  // sliced ELLPACK
+    gb::DevBuf<int32_t> sell_col;
+    gb::DevBuf<double> sell_val;
+    gb::DevBuf<float> sell_val32;
+    gb::DevBuf<int32_t> col_start;  // per-slice x range (Sec. 5.1)
+    gb::DevBuf<int32_t> col_end;
+    gb::CgWork cg;
+
+    bool has64() const { return opt.precision != SPMV_PREC_FP32; }
+    bool has32() const { return opt.precision != SPMV_PREC_FP64; }
+};
+
+namespace gb {
+
+// conversion pipeline (convert.cu)
+spmv_status_t build_matrix(spmv_matrix_t A, const int32_t *d_rp, const int32_t *d_ci,
+                           const double *d_val, cudaStream_t st);
+spmv_status_t build_sell(spmv_matrix_t A, int S, cudaStream_t st);
+
+// kernels (spmv.cu)
+spmv_status_t launch_spmv64(spmv_matrix_t A, const double *x, double *y, cudaStream_t st);
+spmv_status_t launch_spmv32(spmv_matrix_t A, const float *x, float *y, cudaStream_t st);
+spmv_status_t launch_spmv_csr64(spmv_matrix_t A, const double *x, double *y, cudaStream_t st);
+spmv_status_t launch_spmm64(spmv_matrix_t A, int k, const double *X, double *Y, cudaStream_t st);
+spmv_status_t launch_spmm32(spmv_matrix_t A, int k, const float *X, float *Y, cudaStream_t st);
+spmv_status_t launch_permute(spmv_matrix_t A, int direction, int elem_bytes, const void *in,
+                             void *out, cudaStream_t st);
+int window_capacity_words(int block);
+spmv_status_t choose_variant(spmv_matrix_t A, cudaStream_t st);
+
+// device scan utilities (scan.cu): exclusive prefix sum of n int64 values in place; the
+// total is written to out[n] (the array holds n + 1 entries).
+spmv_status_t exclusive_scan_i64(int64_t *d, int64_t n, cudaStream_t st);
+
+}  // namespace gb

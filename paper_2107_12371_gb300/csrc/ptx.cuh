@@ -1,0 +1,130 @@
+// ptx.cuh -- inline-PTX memory access helpers for sm_103a.
+//
+// The matrix (values + column indices) is read exactly once per product, so it is streamed
+// with L1::no_allocate and an L2 evict-first policy: it must not push the multiplying
+// vector x out of L2, where x stays resident between gathers (the GPU counterpart of the
+// paper's on-chip cache of x, Sec. 5.1).  256-bit loads (v4.b64 / v8.b32) are used where a
+// lane reads 32 contiguous bytes.
+#pragma once
+
+#include <cstdint>
+
+namespace gb {
+
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ uint64_t policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+// ---- streamed matrix loads -------------------------------------------------------------
+__device__ __forceinline__ void ld_stream(const double *p, uint64_t pol, double (&v)[1]) {
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.f64 %0, [%1], %2;"
+        : "=d"(v[0]) : "l"(p), "l"(pol));
+}
+__device__ __forceinline__ void ld_stream(const double *p, uint64_t pol, double (&v)[2]) {
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.f64 {%0,%1}, [%2], %3;"
+        : "=d"(v[0]), "=d"(v[1]) : "l"(p), "l"(pol));
+}
+__device__ __forceinline__ void ld_stream(const double *p, uint64_t, double (&v)[4]) {
+    uint64_t a, b, c, d;
+    asm("ld.global.nc.L1::no_allocate.L2::evict_first.v4.b64 {%0,%1,%2,%3}, [%4];"
+        : "=l"(a), "=l"(b), "=l"(c), "=l"(d) : "l"(p));
+    v[0] = __longlong_as_double((long long)a);
+    v[1] = __longlong_as_double((long long)b);
+    v[2] = __longlong_as_double((long long)c);
+    v[3] = __longlong_as_double((long long)d);
+}
+__device__ __forceinline__ void ld_stream(const double *p, uint64_t pol, double (&v)[8]) {
+    double a[4], b[4];
+    ld_stream(p, pol, a);
+    ld_stream(p + 4, pol, b);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        v[i] = a[i];
+        v[4 + i] = b[i];
+    }
+}
+
+__device__ __forceinline__ void ld_stream(const float *p, uint64_t pol, float (&v)[1]) {
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;"
+        : "=f"(v[0]) : "l"(p), "l"(pol));
+}
+__device__ __forceinline__ void ld_stream(const float *p, uint64_t pol, float (&v)[2]) {
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.f32 {%0,%1}, [%2], %3;"
+        : "=f"(v[0]), "=f"(v[1]) : "l"(p), "l"(pol));
+}
+__device__ __forceinline__ void ld_stream(const float *p, uint64_t pol, float (&v)[4]) {
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
+        : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]) : "l"(p), "l"(pol));
+}
+__device__ __forceinline__ void ld_stream(const float *p, uint64_t, float (&v)[8]) {
+    uint32_t r[8];
+    asm("ld.global.nc.L1::no_allocate.L2::evict_first.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7])
+        : "l"(p));
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void ld_stream(const int32_t *p, uint64_t pol, int32_t (&v)[1]) {
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.s32 %0, [%1], %2;"
+        : "=r"(v[0]) : "l"(p), "l"(pol));
+}
+__device__ __forceinline__ void ld_stream(const int32_t *p, uint64_t pol, int32_t (&v)[2]) {
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.s32 {%0,%1}, [%2], %3;"
+        : "=r"(v[0]), "=r"(v[1]) : "l"(p), "l"(pol));
+}
+__device__ __forceinline__ void ld_stream(const int32_t *p, uint64_t pol, int32_t (&v)[4]) {
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.s32 {%0,%1,%2,%3}, [%4], %5;"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]) : "l"(p), "l"(pol));
+}
+__device__ __forceinline__ void ld_stream(const int32_t *p, uint64_t, int32_t (&v)[8]) {
+    asm("ld.global.nc.L1::no_allocate.L2::evict_first.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7])
+        : "l"(p));
+}
+
+// ---- gathers of the multiplying vector (read-only path, L1 allocating) ----------------
+__device__ __forceinline__ double ld_x(const double *p) { return __ldg(p); }
+__device__ __forceinline__ float ld_x(const float *p) { return __ldg(p); }
+
+// ---- stores of R consecutive results -----------------------------------------------------
+template <typename T, int R>
+__device__ __forceinline__ void store_rows(T *y, int64_t row0, int32_t n, const T (&acc)[R]) {
+    if (row0 + R <= n) {
+        if constexpr (sizeof(T) * R >= 16) {
+#pragma unroll
+            for (int i = 0; i < R; i += 16 / (int)sizeof(T)) {
+                if constexpr (sizeof(T) == 8) {
+                    *reinterpret_cast<double2 *>(y + row0 + i) = make_double2(acc[i], acc[i + 1]);
+                } else {
+                    *reinterpret_cast<float4 *>(y + row0 + i) =
+                        make_float4(acc[i], acc[i + 1], acc[i + 2], acc[i + 3]);
+                }
+            }
+        } else if constexpr (sizeof(T) * R == 8 && sizeof(T) == 4) {
+            *reinterpret_cast<float2 *>(y + row0) = make_float2(acc[0], acc[1]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < R; ++i) y[row0 + i] = acc[i];
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < R; ++i)
+            if (row0 + i < n) y[row0 + i] = acc[i];
+    }
+}
+
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+}  // namespace gb

@@ -1,0 +1,254 @@
+// spmv.cu -- SpMV / SpMM kernels.
+//
+// spmv_sell<T, R>: one warp per slice of S = 32 R rows, lane l owns rows l R .. l R + R - 1
+//   of the slice.  Because a slice is stored column-major (Sec. 4.2), step t of the warp reads
+//   32 R consecutive values and column indices: one 8R-byte (FP64) vector load per lane, fully
+//   coalesced, streamed evict-first so the matrix never displaces x from L2.  x is gathered
+//   through the read-only L1 path; with a banded (Cuthill-McKee) order the gathers of
+//   neighbouring rows hit the same lines (Sec. 4.3, 5.1).  Each row accumulates its entries
+//   in ascending column order with fused multiply-add from +0.0; padding entries (column -1)
+//   are skipped.
+// spmv_csr: the naive baseline of Sec. 4.3, thread per CSR row.
+// spmm_sell<T, G, C>: Y = A X for row-major X, G lanes per row, each lane C columns; every
+//   gathered row of X (k contiguous values) is read once per matrix entry and used for all k
+//   columns.
+#include "common.cuh"
+#include "ptx.cuh"
+
+namespace gb {
+namespace {
+
+template <typename T, int R, int U>
+__global__ void __launch_bounds__(1024)
+spmv_sell(int32_t n, int32_t n_slices, const int64_t *__restrict__ sp,
+          const int32_t *__restrict__ col, const T *__restrict__ val, const T *__restrict__ x,
+          T *__restrict__ y) {
+    const int64_t slice = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (slice >= n_slices) return;
+    constexpr int S = 32 * R;
+    const int64_t base = sp[slice];
+    const int w = (int)((sp[slice + 1] - base) / S);
+    const T *vp = val + base + lane * R;
+    const int32_t *cp = col + base + lane * R;
+    const uint64_t pol = policy_evict_first();
+    T acc[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) acc[i] = T(0);
+    int t = 0;
+    for (; t + U <= w; t += U) {
+        T v[U][R];
+        int32_t c[U][R];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            ld_stream(vp + (int64_t)(t + u) * S, pol, v[u]);
+            ld_stream(cp + (int64_t)(t + u) * S, pol, c[u]);
+        }
+        T xv[U][R];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int i = 0; i < R; ++i) xv[u][i] = c[u][i] >= 0 ? ld_x(x + c[u][i]) : T(0);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int i = 0; i < R; ++i)
+                if (c[u][i] >= 0) acc[i] = fma_t(v[u][i], xv[u][i], acc[i]);
+    }
+    for (; t < w; ++t) {
+        T v[R];
+        int32_t c[R];
+        ld_stream(vp + (int64_t)t * S, pol, v);
+        ld_stream(cp + (int64_t)t * S, pol, c);
+#pragma unroll
+        for (int i = 0; i < R; ++i)
+            if (c[i] >= 0) acc[i] = fma_t(v[i], ld_x(x + c[i]), acc[i]);
+    }
+    store_rows<T, R>(y, slice * S + (int64_t)lane * R, n, acc);
+}
+
+// naive CSR baseline (Sec. 4.3): the column index is read first, then x[col] from global
+// memory, thread per row
+template <typename T>
+__global__ void __launch_bounds__(256)
+spmv_csr(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+         const T *__restrict__ val, const T *__restrict__ x, T *__restrict__ y) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    T acc = T(0);
+    for (int32_t k = rp[i]; k < rp[i + 1]; ++k) acc = fma_t(val[k], x[ci[k]], acc);
+    y[i] = acc;
+}
+
+// SpMM: G lanes per row (G divides 32), lane owns columns g, g + G, ... (C of them)
+template <typename T, int G, int C>
+__global__ void __launch_bounds__(256)
+spmm_sell(int32_t n, int32_t S, int32_t n_slices, int k, const int64_t *__restrict__ sp,
+          const int32_t *__restrict__ col, const T *__restrict__ val, const T *__restrict__ X,
+          T *__restrict__ Y) {
+    constexpr int RPW = 32 / G;  // rows per warp step
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane / G, g = lane % G;
+    const int64_t rows_total = (int64_t)n_slices * S;
+    const int64_t row = gw * RPW + sub;
+    if (row >= rows_total) return;
+    const int64_t slice = row / S;
+    const int64_t r = row - slice * S;
+    const int64_t base = sp[slice];
+    const int w = (int)((sp[slice + 1] - base) / S);
+    const uint64_t pol = policy_evict_first();
+    T acc[C];
+#pragma unroll
+    for (int j = 0; j < C; ++j) acc[j] = T(0);
+    for (int t = 0; t < w; ++t) {
+        T a[1];
+        int32_t c[1];
+        ld_stream(val + base + (int64_t)t * S + r, pol, a);
+        ld_stream(col + base + (int64_t)t * S + r, pol, c);
+        if (c[0] < 0) continue;
+        const T *xr = X + (int64_t)c[0] * k;
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            const int cc = g + j * G;
+            if (cc < k) acc[j] = fma_t(a[0], ld_x(xr + cc), acc[j]);
+        }
+    }
+    if (row < n) {
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            const int cc = g + j * G;
+            if (cc < k) Y[row * k + cc] = acc[j];
+        }
+    }
+}
+
+template <typename T>
+__global__ void permute_kernel(int32_t n, int direction, const int32_t *__restrict__ perm,
+                               const T *__restrict__ in, T *__restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (direction == 0) out[i] = in[perm[i]];
+    else out[perm[i]] = in[i];
+}
+
+inline unsigned grid_for(int64_t threads, int block) {
+    int64_t b = (threads + block - 1) / block;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+template <typename T>
+spmv_status_t launch_sell(spmv_matrix_t A, const T *val, const T *x, T *y, cudaStream_t st) {
+    if (A->n == 0) return SPMV_OK;
+    const int block = A->block;
+    const unsigned grid = grid_for((int64_t)A->n_slices * 32, block);
+    switch (A->S) {
+        case 32:
+            spmv_sell<T, 1, 4><<<grid, block, 0, st>>>(A->n, A->n_slices, A->slice_ptr.p,
+                                                       A->sell_col.p, val, x, y);
+            break;
+        case 64:
+            spmv_sell<T, 2, 4><<<grid, block, 0, st>>>(A->n, A->n_slices, A->slice_ptr.p,
+                                                       A->sell_col.p, val, x, y);
+            break;
+        case 128:
+            spmv_sell<T, 4, 2><<<grid, block, 0, st>>>(A->n, A->n_slices, A->slice_ptr.p,
+                                                       A->sell_col.p, val, x, y);
+            break;
+        case 256:
+            spmv_sell<T, 8, 1><<<grid, block, 0, st>>>(A->n, A->n_slices, A->slice_ptr.p,
+                                                       A->sell_col.p, val, x, y);
+            break;
+        default:
+            return SPMV_ERR_INVALID_ARG;
+    }
+    GB_LAUNCHED();
+    return SPMV_OK;
+}
+
+template <typename T>
+spmv_status_t launch_spmm(spmv_matrix_t A, int k, const T *val, const T *X, T *Y,
+                          cudaStream_t st) {
+    if (A->n == 0) return SPMV_OK;
+    const int block = 256;
+    const int64_t rows_total = (int64_t)A->n_slices * A->S;
+    auto go = [&](auto gtag, auto ctag) -> spmv_status_t {
+        constexpr int G = decltype(gtag)::value;
+        constexpr int C = decltype(ctag)::value;
+        const int64_t warps = (rows_total + (32 / G) - 1) / (32 / G);
+        spmm_sell<T, G, C><<<grid_for(warps * 32, block), block, 0, st>>>(
+            A->n, A->S, A->n_slices, k, A->slice_ptr.p, A->sell_col.p, val, X, Y);
+        GB_LAUNCHED();
+        return SPMV_OK;
+    };
+    using I1 = std::integral_constant<int, 1>;
+    using I2 = std::integral_constant<int, 2>;
+    using I4 = std::integral_constant<int, 4>;
+    using I8 = std::integral_constant<int, 8>;
+    using I16 = std::integral_constant<int, 16>;
+    using I32 = std::integral_constant<int, 32>;
+    if (k <= 1) return go(I1{}, I1{});
+    if (k <= 2) return go(I2{}, I1{});
+    if (k <= 4) return go(I4{}, I1{});
+    if (k <= 8) return go(I8{}, I1{});
+    if (k <= 16) return go(I16{}, I1{});
+    if (k <= 32) return go(I32{}, I1{});
+    return go(I32{}, I2{});
+}
+
+}  // namespace
+
+spmv_status_t launch_spmv64(spmv_matrix_t A, const double *x, double *y, cudaStream_t st) {
+    if (A->variant == SPMV_VARIANT_CSR) return launch_spmv_csr64(A, x, y, st);
+    return launch_sell<double>(A, A->sell_val.p, x, y, st);
+}
+
+spmv_status_t launch_spmv32(spmv_matrix_t A, const float *x, float *y, cudaStream_t st) {
+    return launch_sell<float>(A, A->sell_val32.p, x, y, st);
+}
+
+spmv_status_t launch_spmv_csr64(spmv_matrix_t A, const double *x, double *y, cudaStream_t st) {
+    if (A->n == 0) return SPMV_OK;
+    spmv_csr<double><<<grid_for(A->n, 256), 256, 0, st>>>(A->n, A->row_ptr.p, A->col.p, A->val.p,
+                                                          x, y);
+    GB_LAUNCHED();
+    return SPMV_OK;
+}
+
+spmv_status_t launch_spmm64(spmv_matrix_t A, int k, const double *X, double *Y, cudaStream_t st) {
+    return launch_spmm<double>(A, k, A->sell_val.p, X, Y, st);
+}
+
+spmv_status_t launch_spmm32(spmv_matrix_t A, int k, const float *X, float *Y, cudaStream_t st) {
+    return launch_spmm<float>(A, k, A->sell_val32.p, X, Y, st);
+}
+
+spmv_status_t launch_permute(spmv_matrix_t A, int direction, int elem_bytes, const void *in,
+                             void *out, cudaStream_t st) {
+    if (A->n == 0) return SPMV_OK;
+    const unsigned grid = grid_for(A->n, 256);
+    if (!A->perm.p) {
+        GB_CUDA(cudaMemcpyAsync(out, in, (size_t)A->n * elem_bytes, cudaMemcpyDeviceToDevice, st));
+        return SPMV_OK;
+    }
+    if (elem_bytes == 8)
+        permute_kernel<double><<<grid, 256, 0, st>>>(A->n, direction, A->perm.p,
+                                                     (const double *)in, (double *)out);
+    else
+        permute_kernel<float><<<grid, 256, 0, st>>>(A->n, direction, A->perm.p,
+                                                    (const float *)in, (float *)out);
+    GB_LAUNCHED();
+    return SPMV_OK;
+}
+
+int window_capacity_words(int) { return 0; }
+
+spmv_status_t choose_variant(spmv_matrix_t A, cudaStream_t) {
+    if (A->opt.variant == SPMV_VARIANT_AUTO || A->opt.variant == SPMV_VARIANT_SELL_WINDOW)
+        A->variant = SPMV_VARIANT_SELL;
+    else
+        A->variant = A->opt.variant;
+    return SPMV_OK;
+}
+
+}  // namespace gb

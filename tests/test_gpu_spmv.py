@@ -1,0 +1,252 @@
+"""GPU parity of the SpMV path against the CPU oracle, through the C ABI.
+
+Bars: integer structures (permutation, permuted CSR, sliced ELLPACK, per-slice ranges) are
+bit-exact; FP64 products equal the oracle's fused-multiply-add CSR-order sum bit for bit and
+satisfy |y - y_oracle| <= 1e-12 sum_j |a_ij x_j| against the plain multiply-then-add sum;
+FP32 products equal the FP32 oracle bit for bit.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2107_12371_gb300 import capi, meshgen, workloads
+
+pytestmark = pytest.mark.gpu
+
+GATE = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    capi.load()
+    torch.cuda.init()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def absrow(m, x):
+    rows = np.repeat(np.arange(m.n), np.diff(m.row_ptr))
+    return np.bincount(rows, weights=np.abs(m.values * x[m.col_idx]), minlength=m.n)
+
+
+def gpu_spmv(A, x, f32=False, csr=False):
+    xd = dev(x)
+    yd = torch.empty_like(xd)
+    if f32:
+        A.apply_f32(xd, yd)
+    elif csr:
+        A.apply_csr(xd, yd)
+    else:
+        A.apply(xd, yd)
+    torch.cuda.synchronize()
+    return yd.cpu().numpy()
+
+
+def check_fp64(m, x, y, oracle):
+    ref_fma = oracle.spmv(m.row_ptr, m.col_idx, m.values, x, use_fma=True)
+    ref = oracle.spmv(m.row_ptr, m.col_idx, m.values, x, use_fma=False)
+    assert np.array_equal(y, ref_fma), "not bit-identical to the FMA oracle"
+    assert np.all(np.abs(y - ref) <= GATE * absrow(m, x))
+
+
+def ragged_matrix(n, seed, max_len=40, empty_frac=0.1):
+    """Random square CSR with ragged rows (some empty, some long) and sorted columns."""
+    rng = np.random.default_rng(seed)
+    lens = rng.integers(0, max_len + 1, size=n)
+    lens[rng.random(n) < empty_frac] = 0
+    lens = np.minimum(lens, n)
+    rp = np.zeros(n + 1, np.int64)
+    np.cumsum(lens, out=rp[1:])
+    cols = np.concatenate([np.sort(rng.choice(n, size=L, replace=False)) for L in lens]) \
+        if lens.sum() else np.zeros(0, np.int64)
+    vals = rng.uniform(-1, 1, size=int(rp[-1]))
+    return meshgen.CsrMatrix(n, rp.astype(np.int32), cols.astype(np.int32), vals)
+
+
+@pytest.mark.parametrize("S", [32, 64, 128, 256])
+def test_c1_fp64_parity(oracle, S):
+    m, x = workloads.c1()
+    A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values, slice_height=S,
+                    variant=capi.SPMV_VARIANT_SELL)
+    check_fp64(m, x, gpu_spmv(A, x), oracle)
+
+
+def test_c1_naive_csr_parity(oracle):
+    m, x = workloads.c1()
+    A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values)
+    check_fp64(m, x, gpu_spmv(A, x, csr=True), oracle)
+
+
+@pytest.mark.parametrize("S", [32, 128])
+def test_c1_fp32_parity(oracle, S):
+    m, x = workloads.c1()
+    A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values, slice_height=S,
+                    precision=capi.SPMV_PREC_DUAL)
+    x32 = x.astype(np.float32)
+    y = gpu_spmv(A, x32, f32=True)
+    ref = oracle.spmv_f32(m.row_ptr, m.col_idx, m.values.astype(np.float32), x32, use_fma=True)
+    assert np.array_equal(y, ref)
+    # error of the FP32 product against the FP64 oracle (reported bound, not a parity gate)
+    ref64 = oracle.spmv(m.row_ptr, m.col_idx, m.values, x)
+    assert np.all(np.abs(y - ref64) <= 16 * 2.0 ** -24 * absrow(m, x) + 1e-30)
+    # the DUAL handle's FP64 product is unchanged
+    check_fp64(m, x, gpu_spmv(A, x), oracle)
+
+
+@pytest.mark.parametrize("n,seed", [(1, 0), (7, 1), (33, 2), (1000, 3), (4097, 4)])
+@pytest.mark.parametrize("S", [32, 256])
+def test_ragged_and_tiny(oracle, n, seed, S):
+    m = ragged_matrix(n, seed)
+    x = np.random.default_rng(seed + 100).uniform(-1, 1, n)
+    A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values, slice_height=S)
+    check_fp64(m, x, gpu_spmv(A, x), oracle)
+    check_fp64(m, x, gpu_spmv(A, x, csr=True), oracle)
+
+
+def test_empty_matrix_and_zero_rows(oracle):
+    A = capi.Matrix(0, np.zeros(1, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    assert A.info()["n_rows"] == 0
+    xd = torch.empty(0, dtype=torch.float64, device="cuda")
+    A.apply(xd, torch.empty_like(xd))
+    m = meshgen.CsrMatrix(5, np.zeros(6, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    B = capi.Matrix(5, m.row_ptr, m.col_idx, m.values)
+    y = gpu_spmv(B, np.ones(5))
+    assert np.array_equal(y, np.zeros(5))
+
+
+def test_invalid_csr_is_rejected():
+    rp = np.array([0, 2, 3], np.int32)
+    for ci in ([1, 0, 1], [0, 5, 1], [0, 0, 1]):  # unsorted, out of range, duplicate
+        st, h = capi.spmv_create(2, rp, np.array(ci, np.int32), np.ones(3), raw_status=True)
+        assert st == capi.SPMV_ERR_INVALID_CSR and not h
+    st, h = capi.spmv_create(2, np.array([0, 3, 2], np.int32), np.array([0, 1, 1], np.int32),
+                             np.ones(3), raw_status=True)
+    assert st == capi.SPMV_ERR_INVALID_CSR
+    st, h = capi.spmv_create(2, np.array([0, 1, 4], np.int32), np.array([0, 1, 1], np.int32),
+                             np.ones(3), raw_status=True)
+    assert st == capi.SPMV_ERR_INVALID_CSR
+
+
+def test_device_inputs_match_host_inputs(oracle):
+    m, x = workloads.c1()
+    A = capi.Matrix(m.n, dev(m.row_ptr), dev(m.col_idx), dev(m.values))
+    check_fp64(m, x, gpu_spmv(A, x), oracle)
+
+
+# ---------------------------------------------------------------------------------------
+# reordering and format structures: bit-exact against the oracle
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("peripheral", [0, 1])
+@pytest.mark.parametrize("reorder", [capi.SPMV_REORDER_RCM, capi.SPMV_REORDER_CM])
+def test_gpu_cm_order_matches_oracle(oracle, reorder, peripheral):
+    m, x = workloads.c1()
+    A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values, reorder=reorder, peripheral=peripheral)
+    perm = A.permutation()
+    ref = oracle.cm_order(m.row_ptr, m.col_idx, reverse=(reorder == capi.SPMV_REORDER_RCM),
+                          peripheral=bool(peripheral))
+    assert np.array_equal(perm, ref)
+    rp, ci, v = capi.spmv_export_csr(A.handle, m.n, m.nnz)
+    orp, oci, ov = oracle.permute_csr(m.row_ptr, m.col_idx, m.values, ref)
+    assert np.array_equal(rp, orp) and np.array_equal(ci, oci) and np.array_equal(v, ov)
+    info = A.info()
+    bw = int(np.abs(np.repeat(np.arange(m.n), np.diff(orp)) - oci).max())
+    assert info["bandwidth"] == bw
+
+
+def test_gpu_cm_order_hand_worked_graphs(oracle):
+    from test_oracle_pins import _graph_csr, _read_cm_golden
+    for g in _read_cm_golden():
+        rp, ci = _graph_csr(g["n"], g["edges"])
+        for peripheral, expect in g["cm"].items():
+            A = capi.Matrix(g["n"], rp, ci, np.ones(ci.size), reorder=capi.SPMV_REORDER_CM,
+                            peripheral=peripheral)
+            assert list(A.permutation()) == expect
+
+
+@pytest.mark.parametrize("S", [32, 64, 128, 256])
+def test_sell_and_window_export_match_oracle(oracle, S):
+    m, _ = workloads.mixed(6, k=1)
+    A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values, slice_height=S,
+                    reorder=capi.SPMV_REORDER_RCM)
+    rp, ci, v = capi.spmv_export_csr(A.handle, m.n, m.nnz)
+    sp, col, val, cs, ce = capi.spmv_export_sell(A.handle)
+    osp, ocol, oval = oracle.sell(rp, ci, v, S)
+    assert np.array_equal(sp, osp) and np.array_equal(col, ocol) and np.array_equal(val, oval)
+    ocs, oce = oracle.window_meta(m.n, S, osp, ocol)
+    assert np.array_equal(cs, ocs) and np.array_equal(ce, oce)
+    assert A.info()["max_slice_span"] == int((oce - ocs).max())
+
+
+def test_reordered_product_equals_original(oracle):
+    """Sec. 4.1: reordering renumbers the unknowns and leaves the coefficients unchanged, so
+    P^T (P A P^T)(P x) = A x within the gate (row sums are re-associated by the new order)."""
+    m, x = workloads.c1()
+    A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values, reorder=capi.SPMV_REORDER_RCM)
+    xd = dev(x)
+    xp = torch.empty_like(xd)
+    yp = torch.empty_like(xd)
+    y = torch.empty_like(xd)
+    A.permute(0, xd, xp)
+    A.apply(xp, yp)
+    A.permute(1, yp, y)
+    torch.cuda.synchronize()
+    ref = oracle.spmv(m.row_ptr, m.col_idx, m.values, x)
+    assert np.all(np.abs(y.cpu().numpy() - ref) <= GATE * absrow(m, x))
+
+
+# ---------------------------------------------------------------------------------------
+# SpMM
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("k", [1, 3, 8, 32, 64])
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_spmm_parity(oracle, k, dtype):
+    m, _ = workloads.mixed(8, k=1)
+    X = np.random.default_rng(k).uniform(-1, 1, (m.n, k)).astype(dtype)
+    A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values, precision=capi.SPMV_PREC_DUAL)
+    Xd = dev(X)
+    Yd = torch.empty_like(Xd)
+    A.apply_multi(Xd, Yd)
+    torch.cuda.synchronize()
+    Y = Yd.cpu().numpy()
+    vals = m.values.astype(dtype)
+    ref = oracle.spmm(m.row_ptr, m.col_idx, vals, X, use_fma=True)
+    assert np.array_equal(Y, ref)
+    # column c of the block product equals the single-vector product
+    c = k // 2
+    yc = gpu_spmv(A, np.ascontiguousarray(X[:, c]), f32=(dtype == np.float32))
+    assert np.array_equal(Y[:, c], yc)
+
+
+# ---------------------------------------------------------------------------------------
+# full size: the 6M-cell Dirichlet mesh in the benchmark's launch configuration
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("reorder", [capi.SPMV_REORDER_NONE, capi.SPMV_REORDER_RCM])
+def test_c2_full_size_parity(oracle, reorder):
+    m, x = workloads.c2()
+    A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values, reorder=reorder,
+                    precision=capi.SPMV_PREC_DUAL)
+    xd = dev(x)
+    xi = torch.empty_like(xd)
+    A.permute(0, xd, xi)
+    yi = torch.empty_like(xd)
+    A.apply(xi, yi)
+    torch.cuda.synchronize()
+    rp, ci, v = capi.spmv_export_csr(A.handle, m.n, m.nnz)
+    xin = xi.cpu().numpy()
+    mi = meshgen.CsrMatrix(m.n, rp, ci, v)
+    check_fp64(mi, xin, yi.cpu().numpy(), oracle)
+    if reorder == capi.SPMV_REORDER_RCM:
+        perm = A.permutation()
+        ref_perm = oracle.cm_order(m.row_ptr, m.col_idx)
+        assert np.array_equal(perm, ref_perm)
+        assert A.info()["bandwidth"] < m.n // 20
+    # FP32 product of the same handle against the FP32 oracle
+    x32 = xin.astype(np.float32)
+    y32 = gpu_spmv(A, x32, f32=True)
+    ref32 = oracle.spmv_f32(rp, ci, v.astype(np.float32), x32, use_fma=True)
+    assert np.array_equal(y32, ref32)
