@@ -1,23 +1,516 @@
 // cg.cu -- Jacobi-preconditioned conjugate gradients (FP64) and FP32-inner / FP64-refinement
-// solves on top of the SpMV kernels.
-#include "common.cuh"
+// solves built on the sliced-ELLPACK product.  Neither solver is in the paper; the paper puts
+// the SpMV at the heart of the linear solver of an incompressible-flow time step (Sec. 2).
+//
+// One CG iteration is three kernels, each a grid-stride sweep over a fixed grid:
+//   cg_spmv_pq   q = A p and p.q                      -> alpha = rho / (p.q)
+//   cg_update_xr x += alpha p, r -= alpha q, r.(D^-1 r), r.r -> beta, rho, convergence
+//   cg_update_p  p = D^-1 r + beta p
+// Every kernel ends with a deterministic reduction: each CTA writes its partial sums, the
+// last CTA to arrive (atomic ticket) reduces all partials in a fixed order and computes the
+// scalars the next kernel reads.  Results therefore do not depend on CTA scheduling.  A
+// "done" flag set by that last CTA turns the remaining kernels of a CUDA-graph batch into
+// no-ops, so the host only checks convergence once per batch of iterations.
+#include <chrono>
+#include <cmath>
+
+#include "cgkern.cuh"
 
 namespace gb {
+
+namespace {
+
+constexpr int kMaxParts = 4;
+
+// ---- Jacobi diagonal ---------------------------------------------------------------------
+__global__ void cg_dinv(int32_t n, const int32_t *rp, const int32_t *ci, const double *val,
+                        double *dinv64, float *dinv32, int *err) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double d = 0.0;
+    for (int32_t k = rp[i]; k < rp[i + 1]; ++k)
+        if (ci[k] == (int32_t)i) d = val[k];
+    if (d == 0.0) {
+        atomicOr(err, 1);
+        return;
+    }
+    if (dinv64) dinv64[i] = 1.0 / d;
+    if (dinv32) {
+        const float d32 = __double2float_rn(d);
+        if (d32 == 0.0f) atomicOr(err, 1);
+        else dinv32[i] = 1.0f / d32;
+    }
+}
+
+// r = b - A x (x_zero: r = b), p = D^-1 r (if p), partials r.(D^-1 r), r.r, b.b.
+// Last CTA: rho, rr, bb, s = ||r||, done = rr <= tol2 bb.  Used to start and to restart CG,
+// and for the FP64 residual of iterative refinement (p == nullptr).
+template <typename T, int R, int L>
+__global__ void __launch_bounds__(kCgBlock)
+cg_residual(int32_t n, int32_t n_slices, const int64_t *sp, const int32_t *col, const T *val,
+            const T *x, int x_zero, const T *b, T *r, T *p, const T *dinv, double *part,
+            CgScalars *sc) {
+    constexpr int S = L * R;
+    const uint64_t pol = policy_evict_first();
+    const int64_t lanes = (int64_t)gridDim.x * blockDim.x;
+    double v[3] = {0.0, 0.0, 0.0};
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < (int64_t)n_slices * L;
+         g += lanes) {
+        const int64_t slice = g / L;
+        const int lane = (int)(g % L);
+        T acc[R];
+        if (x_zero) {
+#pragma unroll
+            for (int i = 0; i < R; ++i) acc[i] = T(0);
+        } else {
+            slice_rows<T, R, L>(slice, lane, sp, col, val, x, pol, acc);
+        }
+        const int64_t row0 = slice * S + (int64_t)lane * R;
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const int64_t row = row0 + i;
+            if (row < n) {
+                const T bi = b[row];
+                const T ri = bi - acc[i];
+                r[row] = ri;
+                const T zi = dinv ? dinv[row] * ri : ri;
+                if (p) p[row] = zi;
+                v[0] += (double)(ri * zi);
+                v[1] += (double)(ri * ri);
+                v[2] += (double)(bi * bi);
+            }
+        }
+    }
+    double tot[3];
+    if (grid_sum_last<3>(v, part, &sc->tickets[0], tot) && threadIdx.x == 0) {
+        sc->rho = tot[0];
+        sc->rr = tot[1];
+        sc->bb = tot[2];
+        sc->s = sqrt(tot[1]);
+        sc->inv_s = tot[1] > 0.0 ? 1.0 / sc->s : 0.0;
+        sc->done = (tot[1] <= sc->tol2 * tot[2]) ? 1 : 0;
+    }
+}
+
+// q = A p; partial p.q; last CTA: alpha = rho / (p.q)
+template <typename T, int R, int L>
+__global__ void __launch_bounds__(kCgBlock)
+cg_spmv_pq(int32_t n, int32_t n_slices, const int64_t *sp, const int32_t *col, const T *val,
+           const T *p, T *q, double *part, CgScalars *sc) {
+    if (sc->done) return;
+    constexpr int S = L * R;
+    const uint64_t pol = policy_evict_first();
+    const int64_t lanes = (int64_t)gridDim.x * blockDim.x;
+    T vt = T(0);
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < (int64_t)n_slices * L;
+         g += lanes) {
+        const int64_t slice = g / L;
+        const int lane = (int)(g % L);
+        T acc[R];
+        slice_rows<T, R, L>(slice, lane, sp, col, val, p, pol, acc);
+        const int64_t row0 = slice * S + (int64_t)lane * R;
+        store_rows<T, R>(q, row0, n, acc);
+#pragma unroll
+        for (int i = 0; i < R; ++i)
+            if (row0 + i < n) vt = fma_t(p[row0 + i], acc[i], vt);
+    }
+    double v[1] = {(double)vt};
+    double tot[1];
+    if (grid_sum_last<1>(v, part, &sc->tickets[1], tot) && threadIdx.x == 0) {
+        if (tot[0] == 0.0 || !isfinite(tot[0])) {
+            sc->done = 3;
+        } else {
+            sc->alpha = sc->rho / tot[0];
+        }
+    }
+}
+
+// x += alpha p; r -= alpha q; partials r.(D^-1 r), r.r; last CTA: beta, rho, convergence
+template <typename T>
+__global__ void __launch_bounds__(kCgBlock)
+cg_update_xr(int32_t n, T *x, T *r, const T *p, const T *q, const T *dinv, double *part,
+             CgScalars *sc) {
+    if (sc->done) return;
+    const T alpha = (T)sc->alpha;
+    T vz = T(0), vr = T(0);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const T xi = fma_t(alpha, p[i], x[i]);
+        const T ri = fma_t(-alpha, q[i], r[i]);
+        x[i] = xi;
+        r[i] = ri;
+        vz = fma_t(ri, dinv[i] * ri, vz);
+        vr = fma_t(ri, ri, vr);
+    }
+    double v[2] = {(double)vz, (double)vr};
+    double tot[2];
+    if (grid_sum_last<2>(v, part, &sc->tickets[2], tot) && threadIdx.x == 0) {
+        const double rho_new = tot[0];
+        sc->beta = rho_new / sc->rho;
+        sc->rho = rho_new;
+        sc->rr = tot[1];
+        sc->iters += 1;
+        if (tot[1] <= sc->tol2 * sc->bb) sc->done = 1;
+        else if (sc->iters >= sc->max_iter) sc->done = 2;
+        else if (!isfinite(tot[1])) sc->done = 3;
+    }
+}
+
+// p = D^-1 r + beta p
+template <typename T>
+__global__ void __launch_bounds__(kCgBlock)
+cg_update_p(int32_t n, const T *r, const T *dinv, T *p, const CgScalars *sc) {
+    if (sc->done) return;
+    const T beta = (T)sc->beta;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        p[i] = fma_t(beta, p[i], dinv[i] * r[i]);
+}
+
+// refinement: right-hand side of the inner solve r32 = fp32(r64 / ||r64||), start of the
+// inner FP32 PCG (d = 0, r_in = r32, p = D32^-1 r32), partials rho, rr0; inner scalars set
+// by the last CTA.
+__global__ void __launch_bounds__(kCgBlock)
+ir_start_inner(int32_t n, const double *r64, const CgScalars *outer, float *r32, float *p32,
+               float *d32, const float *dinv32, double *part, CgScalars *inner) {
+    const double inv_s = outer->inv_s;
+    float vz = 0.0f, vr = 0.0f;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const float ri = __double2float_rn(r64[i] * inv_s);
+        const float zi = dinv32[i] * ri;
+        r32[i] = ri;
+        p32[i] = zi;
+        d32[i] = 0.0f;
+        vz = fmaf(ri, zi, vz);
+        vr = fmaf(ri, ri, vr);
+    }
+    double v[2] = {(double)vz, (double)vr};
+    double tot[2];
+    if (grid_sum_last<2>(v, part, &inner->tickets[3], tot) && threadIdx.x == 0) {
+        inner->rho = tot[0];
+        inner->rr = tot[1];
+        inner->bb = tot[1];
+        inner->iters = 0;
+        inner->done = tot[1] > 0.0 ? 0 : 1;
+    }
+}
+
+// refinement update x += s d (FP64)
+__global__ void ir_update_x(int32_t n, double *x, const float *d32, const CgScalars *outer) {
+    const double s = outer->s;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        x[i] = fma(s, (double)d32[i], x[i]);
+}
+
+__global__ void set_scalars(CgScalars *sc, double tol2, int max_iter) {
+    sc->tol2 = tol2;
+    sc->max_iter = max_iter;
+    sc->iters = 0;
+    sc->done = 0;
+    for (int k = 0; k < 4; ++k) sc->tickets[k] = 0u;
+}
+
+__global__ void add_iters(CgScalars *inner, int *total) { *total += inner->iters; }
+
+}  // namespace
+
+// grid of the CG sweeps: a fixed multiple of the SM count, so the reduction order is fixed
+static int cg_grid() { return device_facts().sm_count * 4; }
+
+spmv_status_t ensure_cg_work(spmv_matrix_t A, bool mixed, cudaStream_t st) {
+    CgWork &w = A->cg;
+    size_t *t = &A->bytes;
+    const size_t n = (size_t)A->n;
+    if (!w.ready) {
+        const int G = cg_grid();
+        w.part_len = G;
+        GB_TRY(w.part.alloc((size_t)G * kMaxParts * 2, t));
+        GB_TRY(w.scal.alloc(2 * ((sizeof(CgScalars) + 7) / 8), t));
+        GB_TRY(w.flags.alloc(16, t));
+        GB_CUDA(cudaMallocHost((void **)&w.h_scal, 2 * sizeof(CgScalars)));
+        GB_CUDA(cudaMallocHost((void **)&w.h_flags, 16 * sizeof(int)));
+        GB_TRY(w.x.alloc(n, t));
+        GB_TRY(w.r.alloc(n, t));
+        GB_TRY(w.p.alloc(n, t));
+        GB_TRY(w.q.alloc(n, t));
+        GB_TRY(w.dinv.alloc(n, t));
+        GB_CUDA(cudaMemsetAsync(w.flags.p, 0, 16 * sizeof(int), st));
+        cg_dinv<<<(unsigned)((n + 255) / 256 ? (n + 255) / 256 : 1), 256, 0, st>>>(
+            A->n, A->row_ptr.p, A->col.p, A->val.p, w.dinv.p, nullptr, w.flags.p);
+        GB_LAUNCHED();
+        w.ready = true;
+    }
+    if (mixed && !w.mixed_ready) {
+        if (!A->has32()) return SPMV_ERR_UNSUPPORTED;
+        GB_TRY(w.r32.alloc(n, t));
+        GB_TRY(w.p32.alloc(n, t));
+        GB_TRY(w.q32.alloc(n, t));
+        GB_TRY(w.d32.alloc(n, t));
+        GB_TRY(w.dinv32.alloc(n, t));
+        cg_dinv<<<(unsigned)((n + 255) / 256 ? (n + 255) / 256 : 1), 256, 0, st>>>(
+            A->n, A->row_ptr.p, A->col.p, A->val.p, nullptr, w.dinv32.p, w.flags.p + 1);
+        GB_LAUNCHED();
+        w.mixed_ready = true;
+    }
+    GB_CUDA(cudaMemcpyAsync(w.h_flags, w.flags.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    GB_CUDA(cudaStreamSynchronize(st));
+    if (w.h_flags[0] || (mixed && w.h_flags[1])) return SPMV_ERR_INVALID_CSR;
+    return SPMV_OK;
+}
+
+static CgScalars *outer_scalars(spmv_matrix_t A) { return (CgScalars *)A->cg.scal.p; }
+static CgScalars *inner_scalars(spmv_matrix_t A) { return (CgScalars *)A->cg.scal.p + 1; }
+
+// enqueue `iters` FP64 iterations (3 kernels each)
+static spmv_status_t enqueue_cg64(spmv_matrix_t A, int iters, cudaStream_t st) {
+    CgWork &w = A->cg;
+    const int G = cg_grid();
+    CgScalars *sc = outer_scalars(A);
+    return with_shape(A->S, false, [&](auto rt, auto lt) -> spmv_status_t {
+        constexpr int R = decltype(rt)::value, L = decltype(lt)::value;
+        for (int it = 0; it < iters; ++it) {
+            cg_spmv_pq<double, R, L><<<G, kCgBlock, 0, st>>>(A->n, A->n_slices, A->slice_ptr.p,
+                                                             A->sell_col.p, A->sell_val.p, w.p.p,
+                                                             w.q.p, w.part.p, sc);
+            cg_update_xr<double><<<G, kCgBlock, 0, st>>>(A->n, w.x.p, w.r.p, w.p.p, w.q.p,
+                                                         w.dinv.p, w.part.p + G, sc);
+            cg_update_p<double><<<G, kCgBlock, 0, st>>>(A->n, w.r.p, w.dinv.p, w.p.p, sc);
+        }
+        GB_LAUNCHED();
+        return SPMV_OK;
+    });
+}
+
+static spmv_status_t enqueue_cg32(spmv_matrix_t A, int iters, cudaStream_t st) {
+    CgWork &w = A->cg;
+    const int G = cg_grid();
+    CgScalars *sc = inner_scalars(A);
+    return with_shape(A->S, true, [&](auto rt, auto lt) -> spmv_status_t {
+        constexpr int R = decltype(rt)::value, L = decltype(lt)::value;
+        for (int it = 0; it < iters; ++it) {
+            cg_spmv_pq<float, R, L><<<G, kCgBlock, 0, st>>>(A->n, A->n_slices, A->slice_ptr.p,
+                                                            A->sell_col.p, A->sell_val32.p,
+                                                            w.p32.p, w.q32.p, w.part.p, sc);
+            cg_update_xr<float><<<G, kCgBlock, 0, st>>>(A->n, w.d32.p, w.r32.p, w.p32.p, w.q32.p,
+                                                        w.dinv32.p, w.part.p + G, sc);
+            cg_update_p<float><<<G, kCgBlock, 0, st>>>(A->n, w.r32.p, w.dinv32.p, w.p32.p, sc);
+        }
+        GB_LAUNCHED();
+        return SPMV_OK;
+    });
+}
+
+// r = b - A x on the FP64 values, p = D^-1 r when want_p
+static spmv_status_t enqueue_residual64(spmv_matrix_t A, const double *b, bool x_zero,
+                                        bool want_p, cudaStream_t st) {
+    CgWork &w = A->cg;
+    const int G = cg_grid();
+    return with_shape(A->S, false, [&](auto rt, auto lt) -> spmv_status_t {
+        constexpr int R = decltype(rt)::value, L = decltype(lt)::value;
+        cg_residual<double, R, L><<<G, kCgBlock, 0, st>>>(
+            A->n, A->n_slices, A->slice_ptr.p, A->sell_col.p, A->sell_val.p, w.x.p,
+            x_zero ? 1 : 0, b, w.r.p, want_p ? w.p.p : nullptr, w.dinv.p, w.part.p, outer_scalars(A));
+        GB_LAUNCHED();
+        return SPMV_OK;
+    });
+}
+
+// Graph of `iters` iterations, captured once per handle and kind.
+static spmv_status_t get_graph(spmv_matrix_t A, bool f32, int iters, cudaGraphExec_t *out) {
+    CgWork &w = A->cg;
+    cudaGraphExec_t &g = f32 ? w.graph32 : w.graph64;
+    int &gi = f32 ? w.graph32_iters : w.graph64_iters;
+    if (g && gi == iters) {
+        *out = g;
+        return SPMV_OK;
+    }
+    if (g) {
+        cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
+    if (!w.cap_stream) GB_CUDA(cudaStreamCreateWithFlags(&w.cap_stream, cudaStreamNonBlocking));
+    GB_CUDA(cudaStreamBeginCapture(w.cap_stream, cudaStreamCaptureModeThreadLocal));
+    spmv_status_t s = f32 ? enqueue_cg32(A, iters, w.cap_stream) : enqueue_cg64(A, iters, w.cap_stream);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(w.cap_stream, &graph);
+    if (s != SPMV_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return s;
+    }
+    GB_CUDA(e);
+    e = cudaGraphInstantiate(&g, graph, 0);
+    cudaGraphDestroy(graph);
+    GB_CUDA(e);
+    gi = iters;
+    *out = g;
+    return SPMV_OK;
+}
+
+using Clock = std::chrono::steady_clock;
+
+static double seconds_since(Clock::time_point t0) {
+    return std::chrono::duration<double>(Clock::now() - t0).count();
+}
+
+// read both scalar blocks to the host
+static spmv_status_t read_scalars(spmv_matrix_t A, cudaStream_t st, CgScalars *outer,
+                                  CgScalars *inner) {
+    CgWork &w = A->cg;
+    GB_CUDA(cudaMemcpyAsync(w.h_scal, w.scal.p, 2 * sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
+    GB_CUDA(cudaStreamSynchronize(st));
+    if (outer) *outer = ((CgScalars *)w.h_scal)[0];
+    if (inner) *inner = ((CgScalars *)w.h_scal)[1];
+    return SPMV_OK;
+}
+
+spmv_status_t cg_persistent64(spmv_matrix_t A, const cg_options_t &o, CgScalars *out,
+                              cudaStream_t st);
+
+// Plain FP64 Jacobi-PCG in the handle's x buffer; x holds x0 (or anything if !use_x0).
+static spmv_status_t solve64(spmv_matrix_t A, const double *b, const cg_options_t &o,
+                             cg_result_t *res, cudaStream_t st, Clock::time_point t0) {
+    CgWork &w = A->cg;
+    const int batch = o.check_every > 0 ? o.check_every : 16;
+    CgScalars *sc = outer_scalars(A);
+    set_scalars<<<1, 1, 0, st>>>(sc, o.rtol * o.rtol, o.max_iter);
+    GB_LAUNCHED();
+    GB_TRY(enqueue_residual64(A, b, !o.use_x0, true, st));
+    CgScalars h{};
+    int restarts = 0;
+    int total_iters = 0;
+    for (;;) {
+        if (o.persistent) {
+            GB_TRY(cg_persistent64(A, o, &h, st));
+        } else {
+            cudaGraphExec_t g;
+            GB_TRY(get_graph(A, false, batch, &g));
+            for (;;) {
+                GB_CUDA(cudaGraphLaunch(g, st));
+                GB_TRY(read_scalars(A, st, &h, nullptr));
+                if (h.done) break;
+                if (o.timeout_s > 0 && seconds_since(t0) > o.timeout_s) break;
+            }
+        }
+        total_iters = h.iters;
+        if (h.done == 0 || h.done == 4) {
+            res->status = SPMV_ERR_TIMEOUT;
+            break;
+        }
+        if (h.done == 2) {
+            res->status = SPMV_ERR_NOT_CONVERGED;
+            break;
+        }
+        if (h.done == 3) {
+            res->status = SPMV_ERR_NOT_CONVERGED;
+            break;
+        }
+        // recurrence converged: recompute the true residual; restart the recurrence from it
+        // if it is still above the tolerance (at most two restarts)
+        GB_TRY(enqueue_residual64(A, b, false, true, st));
+        GB_TRY(read_scalars(A, st, &h, nullptr));
+        if (h.done == 1) {
+            res->status = SPMV_OK;
+            break;
+        }
+        if (restarts >= 2) {
+            res->status = SPMV_ERR_NOT_CONVERGED;
+            break;
+        }
+        ++restarts;
+    }
+    res->iterations = total_iters;
+    res->outer_iterations = restarts;
+    (void)w;
+    return SPMV_OK;
+}
+
+static spmv_status_t solve_mixed(spmv_matrix_t A, const double *b, const cg_options_t &o,
+                                 cg_result_t *res, cudaStream_t st, Clock::time_point t0) {
+    CgWork &w = A->cg;
+    const int batch = o.check_every > 0 ? o.check_every : 16;
+    const int G = cg_grid();
+    CgScalars *so = outer_scalars(A);
+    CgScalars *si = inner_scalars(A);
+    int *d_total = w.flags.p + 4;
+    GB_CUDA(cudaMemsetAsync(d_total, 0, sizeof(int), st));
+    set_scalars<<<1, 1, 0, st>>>(so, o.rtol * o.rtol, 1);
+    GB_LAUNCHED();
+    GB_TRY(enqueue_residual64(A, b, !o.use_x0, false, st));
+    CgScalars ho{}, hi{};
+    GB_TRY(read_scalars(A, st, &ho, nullptr));
+    int outer = 0;
+    res->status = SPMV_OK;
+    while (!ho.done) {
+        if (outer >= o.max_outer) {
+            res->status = SPMV_ERR_NOT_CONVERGED;
+            break;
+        }
+        if (o.timeout_s > 0 && seconds_since(t0) > o.timeout_s) {
+            res->status = SPMV_ERR_TIMEOUT;
+            break;
+        }
+        set_scalars<<<1, 1, 0, st>>>(si, o.inner_rtol * o.inner_rtol, o.max_iter);
+        ir_start_inner<<<G, kCgBlock, 0, st>>>(A->n, w.r.p, so, w.r32.p, w.p32.p, w.d32.p,
+                                               w.dinv32.p, w.part.p, si);
+        GB_LAUNCHED();
+        cudaGraphExec_t g;
+        GB_TRY(get_graph(A, true, batch, &g));
+        for (;;) {
+            GB_CUDA(cudaGraphLaunch(g, st));
+            GB_TRY(read_scalars(A, st, nullptr, &hi));
+            if (hi.done) break;
+            if (o.timeout_s > 0 && seconds_since(t0) > o.timeout_s) break;
+        }
+        add_iters<<<1, 1, 0, st>>>(si, d_total);
+        ir_update_x<<<G, kCgBlock, 0, st>>>(A->n, w.x.p, w.d32.p, so);
+        GB_LAUNCHED();
+        ++outer;
+        GB_TRY(enqueue_residual64(A, b, false, false, st));
+        GB_TRY(read_scalars(A, st, &ho, nullptr));
+        if (hi.done == 0) {
+            res->status = SPMV_ERR_TIMEOUT;
+            break;
+        }
+    }
+    GB_CUDA(cudaMemcpyAsync(w.h_flags + 4, d_total, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GB_CUDA(cudaStreamSynchronize(st));
+    res->iterations = w.h_flags[4];
+    res->outer_iterations = outer;
+    return SPMV_OK;
+}
+
+// true relative residual ||b - A x|| / ||b|| of the handle's x, in FP64
+static spmv_status_t final_residual(spmv_matrix_t A, const double *b, cudaStream_t st,
+                                    double *rel) {
+    CgScalars *sc = outer_scalars(A);
+    set_scalars<<<1, 1, 0, st>>>(sc, 0.0, 1);
+    GB_LAUNCHED();
+    GB_TRY(enqueue_residual64(A, b, false, false, st));
+    CgScalars h{};
+    GB_TRY(read_scalars(A, st, &h, nullptr));
+    *rel = h.bb > 0.0 ? std::sqrt(h.rr / h.bb) : 0.0;
+    return SPMV_OK;
+}
 
 void release_cg(spmv_matrix_t A) {
     size_t *t = &A->bytes;
     CgWork &w = A->cg;
-    w.r.release(t); w.z.release(t); w.p.release(t); w.q.release(t); w.dinv.release(t);
+    w.x.release(t); w.r.release(t); w.p.release(t); w.q.release(t); w.dinv.release(t);
     w.r32.release(t); w.p32.release(t); w.q32.release(t); w.d32.release(t); w.dinv32.release(t);
     w.part.release(t); w.scal.release(t); w.flags.release(t);
     if (w.h_flags) cudaFreeHost(w.h_flags);
     if (w.h_scal) cudaFreeHost(w.h_scal);
-    w.h_flags = nullptr;
-    w.h_scal = nullptr;
-    w.ready = false;
+    if (w.graph64) cudaGraphExecDestroy(w.graph64);
+    if (w.graph32) cudaGraphExecDestroy(w.graph32);
+    if (w.cap_stream) cudaStreamDestroy(w.cap_stream);
+    w = CgWork{};
 }
 
 }  // namespace gb
+
+using namespace gb;
 
 extern "C" {
 
@@ -35,10 +528,45 @@ spmv_status_t cg_default_options(cg_options_t *o) {
     return SPMV_OK;
 }
 
-spmv_status_t cg_solve(spmv_matrix_t A, const double *, double *, const cg_options_t *,
-                       cg_result_t *, void *) {
+spmv_status_t cg_solve(spmv_matrix_t A, const double *b, double *x, const cg_options_t *opt,
+                       cg_result_t *result, void *stream) {
     if (!A) return SPMV_ERR_INVALID_ARG;
-    return SPMV_ERR_UNSUPPORTED;
+    cg_result_t local{};
+    cg_result_t *res = result ? result : &local;
+    *res = cg_result_t{};
+    res->status = SPMV_ERR_INVALID_ARG;
+    if (A->n > 0 && (!b || !x || b == x)) return SPMV_ERR_INVALID_ARG;
+    cg_options_t o;
+    cg_default_options(&o);
+    if (opt) o = *opt;
+    if (!(o.rtol >= 0.0) || o.max_iter < 1 || o.check_every < 0 || o.max_outer < 0 ||
+        !(o.inner_rtol > 0.0 && o.inner_rtol < 1.0) || o.timeout_s < 0)
+        return SPMV_ERR_INVALID_ARG;
+    if (!A->has64()) return (res->status = SPMV_ERR_UNSUPPORTED);
+    if (o.mixed && !A->has32()) return (res->status = SPMV_ERR_UNSUPPORTED);
+    if (A->n == 0) {
+        res->status = SPMV_OK;
+        return SPMV_OK;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const auto t0 = Clock::now();
+    spmv_status_t s = ensure_cg_work(A, o.mixed != 0, st);
+    if (s != SPMV_OK) return (res->status = s);
+    CgWork &w = A->cg;
+    if (o.use_x0) {
+        s = cuda_status(cudaMemcpyAsync(w.x.p, x, sizeof(double) * A->n, cudaMemcpyDeviceToDevice, st));
+        if (s != SPMV_OK) return (res->status = s);
+    }
+    s = o.mixed ? solve_mixed(A, b, o, res, st, t0) : solve64(A, b, o, res, st, t0);
+    if (s != SPMV_OK) return (res->status = s);
+    double rel = 0.0;
+    s = final_residual(A, b, st, &rel);
+    if (s != SPMV_OK) return (res->status = s);
+    res->rel_residual = rel;
+    s = cuda_status(cudaMemcpyAsync(x, w.x.p, sizeof(double) * A->n, cudaMemcpyDeviceToDevice, st));
+    if (s == SPMV_OK) s = cuda_status(cudaStreamSynchronize(st));
+    if (s != SPMV_OK) return (res->status = s);
+    return res->status;
 }
 
 }  // extern "C"

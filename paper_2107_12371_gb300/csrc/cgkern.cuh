@@ -1,0 +1,153 @@
+// cgkern.cuh -- device building blocks shared by the CG kernels (graph-launched and
+// persistent): deterministic reductions, the product rows of one slice, shape dispatch.
+#pragma once
+
+#include <type_traits>
+
+#include "common.cuh"
+#include "ptx.cuh"
+
+namespace gb {
+
+constexpr int kCgBlock = 256;
+
+// Sum over the CTA in a fixed tree; the total is left in every lane of warp 0.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV]) {
+    __shared__ double sh[NV][kCgBlock / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    }
+    __syncthreads();
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) sh[k][warp] = v[k];
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double t = lane < kCgBlock / 32 ? sh[k][lane] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            v[k] = t;
+        }
+    }
+}
+
+// Same sum, broadcast to every thread of the CTA.
+template <int NV>
+__device__ __forceinline__ void block_sum_all(double (&v)[NV]) {
+    __shared__ double bc[NV];
+    block_sum<NV>(v);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) bc[k] = v[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = bc[k];
+    __syncthreads();
+}
+
+// Each CTA stores its partial sums in part[k * gridDim.x + cta]; the CTA that arrives last
+// (atomic ticket) sums all partials in a fixed order.  Returns true in that CTA, with the
+// grid totals in tot[] (valid in thread 0); the ticket is reset for the next launch.
+template <int NV>
+__device__ bool grid_sum_last(double (&v)[NV], double *part, unsigned *ticket, double (&tot)[NV]) {
+    __shared__ bool last;
+    block_sum<NV>(v);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) part[k * gridDim.x + blockIdx.x] = v[k];
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    double s[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        s[k] = 0.0;
+        for (int i = threadIdx.x; i < (int)gridDim.x; i += kCgBlock)
+            s[k] += __ldcg(part + k * gridDim.x + i);
+    }
+    block_sum<NV>(s);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) tot[k] = s[k];
+        *ticket = 0u;
+    }
+    return true;
+}
+
+// y-rows (R of them) of lane `lane` in slice `slice`: sum over the slice's columns in order,
+// fused multiply-add from +0.0, padding skipped (the same order as spmv_sell).
+template <typename T, int R, int L>
+__device__ __forceinline__ void slice_rows(int64_t slice, int lane, const int64_t *sp,
+                                           const int32_t *col, const T *val, const T *x,
+                                           uint64_t pol, T (&acc)[R]) {
+    constexpr int S = L * R;
+    const int64_t base = sp[slice];
+    const int w = (int)((sp[slice + 1] - base) / S);
+    const T *vp = val + base + lane * R;
+    const int32_t *cp = col + base + lane * R;
+#pragma unroll
+    for (int i = 0; i < R; ++i) acc[i] = T(0);
+    int t = 0;
+    for (; t + 2 <= w; t += 2) {
+        T v[2][R];
+        int32_t c[2][R];
+        ld_stream(vp + (int64_t)t * S, pol, v[0]);
+        ld_stream(cp + (int64_t)t * S, pol, c[0]);
+        ld_stream(vp + (int64_t)(t + 1) * S, pol, v[1]);
+        ld_stream(cp + (int64_t)(t + 1) * S, pol, c[1]);
+        T xv[2][R];
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+            for (int i = 0; i < R; ++i) xv[u][i] = c[u][i] >= 0 ? ld_x(x + c[u][i]) : T(0);
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+            for (int i = 0; i < R; ++i)
+                if (c[u][i] >= 0) acc[i] = fma_t(v[u][i], xv[u][i], acc[i]);
+    }
+    for (; t < w; ++t) {
+        T v[R];
+        int32_t c[R];
+        ld_stream(vp + (int64_t)t * S, pol, v);
+        ld_stream(cp + (int64_t)t * S, pol, c);
+#pragma unroll
+        for (int i = 0; i < R; ++i)
+            if (c[i] >= 0) acc[i] = fma_t(v[i], ld_x(x + c[i]), acc[i]);
+    }
+}
+
+// (R, L) of the sliced kernels for a slice height and value type.
+template <typename F>
+spmv_status_t with_shape(int S, bool f32, F &&f) {
+    using std::integral_constant;
+    if (!f32) {
+        switch (S) {
+            case 32: return f(integral_constant<int, 1>{}, integral_constant<int, 32>{});
+            case 64: return f(integral_constant<int, 2>{}, integral_constant<int, 32>{});
+            case 128: return f(integral_constant<int, 4>{}, integral_constant<int, 32>{});
+            case 256: return f(integral_constant<int, 8>{}, integral_constant<int, 32>{});
+        }
+    } else {
+        switch (S) {
+            case 32: return f(integral_constant<int, 4>{}, integral_constant<int, 8>{});
+            case 64: return f(integral_constant<int, 4>{}, integral_constant<int, 16>{});
+            case 128: return f(integral_constant<int, 4>{}, integral_constant<int, 32>{});
+            case 256: return f(integral_constant<int, 8>{}, integral_constant<int, 32>{});
+        }
+    }
+    return SPMV_ERR_INVALID_ARG;
+}
+
+}  // namespace gb

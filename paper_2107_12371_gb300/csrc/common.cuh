@@ -68,17 +68,34 @@ struct DevBuf {
     }
 };
 
+// Device scalars of one CG recurrence (written by the last CTA of a reduction).
+struct CgScalars {
+    double alpha, beta, rho, rr, bb, tol2, s, inv_s;
+    int done;   // 0 running, 1 converged, 2 iteration cap, 3 breakdown, 4 timeout
+    int iters;
+    int max_iter;
+    int pad;
+    unsigned tickets[4];
+    unsigned bar_count, bar_gen;    // grid barrier of the persistent kernel
+    long long budget_ns;            // persistent kernel: wall-clock budget (0 = none)
+};
+
 // Work vectors of a CG solve (allocated on first use, kept with the handle).
 struct CgWork {
-    DevBuf<double> r, z, p, q, dinv;
+    DevBuf<double> x, r, p, q, dinv;
     DevBuf<float> r32, p32, q32, d32, dinv32;
     DevBuf<double> part;        // per-CTA partial sums
-    DevBuf<double> scal;        // device scalars
+    DevBuf<double> scal;        // two CgScalars blocks (outer / inner)
     DevBuf<int> flags;          // status flags
     int *h_flags = nullptr;     // pinned host mirror
     double *h_scal = nullptr;   // pinned host mirror
     int part_len = 0;
     bool ready = false;
+    bool mixed_ready = false;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph64 = nullptr, graph32 = nullptr, graph_pers = nullptr;
+    int graph64_iters = 0, graph32_iters = 0;
+    int pers_grid = 0;
 };
 
 }  // namespace gb

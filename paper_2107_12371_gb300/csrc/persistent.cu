@@ -1,0 +1,207 @@
+// persistent.cu -- the whole FP64 Jacobi-PCG loop in one cooperative kernel.
+//
+// Every CTA of a co-resident grid (cooperative launch) runs the iterations; the three phases
+// of an iteration (q = A p with p.q; x/r update with r.z and r.r; p update) are separated by a
+// grid barrier.  After each barrier every CTA sums the per-CTA partials of the previous phase
+// in the same fixed order, so all CTAs hold bit-identical scalars and take identical branch
+// decisions.  The results equal the graph-launched path's (same per-CTA partitions, same
+// reduction trees).  Every barrier wait is bounded: after 2 s without progress the waiting
+// CTA records done = 4 (timeout) and the whole grid leaves the loop, so a fault can never
+// leave the GPU spinning.
+#include "cgkern.cuh"
+
+namespace gb {
+namespace {
+
+__device__ __forceinline__ long long global_timer_ns() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+constexpr long long kBarrierLimitNs = 2000000000LL;
+
+__device__ bool grid_barrier(CgScalars *sc) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *genp = &sc->bar_gen;
+        const unsigned g = *genp;
+        __threadfence();
+        const unsigned arrived = atomicAdd(&sc->bar_count, 1u);
+        int good = 1;
+        if (arrived == gridDim.x - 1) {
+            atomicExch(&sc->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&sc->bar_gen, 1u);
+        } else {
+            const long long t0 = global_timer_ns();
+            while (*genp == g) {
+                if (global_timer_ns() - t0 > kBarrierLimitNs) {
+                    good = 0;
+                    atomicExch(&sc->done, 4);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// sum of part[k * G + i] over i in a fixed order, broadcast to all threads
+template <int NV>
+__device__ void reduce_parts(const double *part, double (&tot)[NV]) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        tot[k] = 0.0;
+        for (int i = threadIdx.x; i < (int)gridDim.x; i += kCgBlock)
+            tot[k] += __ldcg(part + k * gridDim.x + i);
+    }
+    block_sum_all<NV>(tot);
+}
+
+template <int NV>
+__device__ void store_parts(double (&v)[NV], double *part) {
+    block_sum<NV>(v);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) part[k * gridDim.x + blockIdx.x] = v[k];
+    }
+}
+
+template <int R, int L>
+__global__ void __launch_bounds__(kCgBlock)
+cg_persistent(int32_t n, int32_t n_slices, const int64_t *sp, const int32_t *col,
+              const double *val, double *x, double *r, double *p, double *q, const double *dinv,
+              double *part, CgScalars *sc) {
+    constexpr int S = L * R;
+    const uint64_t pol = policy_evict_first();
+    const long long t_start = global_timer_ns();
+    const long long budget = sc->budget_ns;
+    double rho = sc->rho;
+    const double bb = sc->bb, tol2 = sc->tol2;
+    int iters = sc->iters;
+    const int max_iter = sc->max_iter;
+    int done = sc->done;
+    double *part1 = part;                   // p.q, stop vote
+    double *part2 = part + 2 * gridDim.x;   // r.z, r.r
+    const int64_t lanes = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double beta = 0.0;
+    while (!done) {
+        // phase 1: q = A p, p.q (and CTA 0's vote to stop on the wall-clock budget)
+        double vt = 0.0;
+        for (int64_t g = tid; g < (int64_t)n_slices * L; g += lanes) {
+            const int64_t slice = g / L;
+            const int lane = (int)(g % L);
+            double acc[R];
+            slice_rows<double, R, L>(slice, lane, sp, col, val, p, pol, acc);
+            const int64_t row0 = slice * S + (int64_t)lane * R;
+            store_rows<double, R>(q, row0, n, acc);
+#pragma unroll
+            for (int i = 0; i < R; ++i)
+                if (row0 + i < n) vt = fma(p[row0 + i], acc[i], vt);
+        }
+        double v1[2] = {vt, 0.0};
+        if (blockIdx.x == 0 && threadIdx.x == 0 && budget > 0 &&
+            global_timer_ns() - t_start > budget)
+            v1[1] = 1.0;
+        store_parts<2>(v1, part1);
+        if (!grid_barrier(sc)) {
+            done = 4;
+            break;
+        }
+        double t1[2];
+        reduce_parts<2>(part1, t1);
+        if (t1[1] != 0.0) {
+            done = 4;
+            break;
+        }
+        if (t1[0] == 0.0 || !isfinite(t1[0])) {
+            done = 3;
+            break;
+        }
+        const double alpha = rho / t1[0];
+        // phase 2: x += alpha p, r -= alpha q, r.z, r.r
+        double vz = 0.0, vr = 0.0;
+        for (int64_t i = tid; i < n; i += lanes) {
+            const double xi = fma(alpha, p[i], x[i]);
+            const double ri = fma(-alpha, q[i], r[i]);
+            x[i] = xi;
+            r[i] = ri;
+            vz = fma(ri, dinv[i] * ri, vz);
+            vr = fma(ri, ri, vr);
+        }
+        double v2[2] = {vz, vr};
+        store_parts<2>(v2, part2);
+        if (!grid_barrier(sc)) {
+            done = 4;
+            break;
+        }
+        double t2[2];
+        reduce_parts<2>(part2, t2);
+        beta = t2[0] / rho;
+        rho = t2[0];
+        ++iters;
+        if (t2[1] <= tol2 * bb) done = 1;
+        else if (iters >= max_iter) done = 2;
+        else if (!isfinite(t2[1])) done = 3;
+        if (done) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) sc->rr = t2[1];
+            break;
+        }
+        // phase 3: p = D^-1 r + beta p
+        for (int64_t i = tid; i < n; i += lanes) p[i] = fma(beta, p[i], dinv[i] * r[i]);
+        if (!grid_barrier(sc)) {
+            done = 4;
+            break;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (done == 4) atomicExch(&sc->done, 4);
+        else atomicCAS(&sc->done, 0, done);
+        sc->iters = iters;
+        sc->rho = rho;
+        sc->beta = beta;
+    }
+}
+
+}  // namespace
+
+spmv_status_t cg_persistent64(spmv_matrix_t A, const cg_options_t &o, CgScalars *out,
+                              cudaStream_t st) {
+    CgWork &w = A->cg;
+    CgScalars *sc = (CgScalars *)w.scal.p;
+    return with_shape(A->S, false, [&](auto rt, auto lt) -> spmv_status_t {
+        constexpr int R = decltype(rt)::value, L = decltype(lt)::value;
+        auto kern = cg_persistent<R, L>;
+        if (w.pers_grid == 0) {
+            int per_sm = 0;
+            GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCgBlock, 0));
+            if (per_sm < 1) return SPMV_ERR_UNSUPPORTED;
+            const int G = device_facts().sm_count * (per_sm < 4 ? per_sm : 4);
+            w.pers_grid = G < w.part_len ? G : w.part_len;
+        }
+        const long long budget = o.timeout_s > 0 ? (long long)(o.timeout_s * 1e9) : 0;
+        GB_CUDA(cudaMemcpyAsync(&sc->budget_ns, &budget, sizeof(budget), cudaMemcpyHostToDevice, st));
+        int32_t n = A->n, ns = A->n_slices;
+        const int64_t *sp = A->slice_ptr.p;
+        const int32_t *col = A->sell_col.p;
+        const double *val = A->sell_val.p;
+        double *x = w.x.p, *r = w.r.p, *p = w.p.p, *q = w.q.p, *part = w.part.p;
+        const double *dinv = w.dinv.p;
+        void *args[] = {&n, &ns, &sp, &col, &val, &x, &r, &p, &q, &dinv, &part, &sc};
+        GB_CUDA(cudaLaunchCooperativeKernel((const void *)kern, dim3(w.pers_grid), dim3(kCgBlock),
+                                            args, 0, st));
+        GB_CUDA(cudaMemcpyAsync(w.h_scal, w.scal.p, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
+        GB_CUDA(cudaStreamSynchronize(st));
+        *out = *(CgScalars *)w.h_scal;
+        return SPMV_OK;
+    });
+}
+
+}  // namespace gb

@@ -1,8 +1,8 @@
 // spmv.cu -- SpMV / SpMM kernels.
 //
-// spmv_sell<T, R>: one warp per slice of S = 32 R rows, lane l owns rows l R .. l R + R - 1
-//   of the slice.  Because a slice is stored column-major (Sec. 4.2), step t of the warp reads
-//   32 R consecutive values and column indices: one 8R-byte (FP64) vector load per lane, fully
+// spmv_sell<T, R, L>: L lanes per slice of S = L R rows, lane l owns rows l R .. l R + R - 1
+//   of the slice.  Because a slice is stored column-major (Sec. 4.2), step t of the lanes
+//   reads S consecutive values and column indices: one R-wide vector load per lane, fully
 //   coalesced, streamed evict-first so the matrix never displaces x from L2.  x is gathered
 //   through the read-only L1 path; with a banded (Cuthill-McKee) order the gathers of
 //   neighbouring rows hit the same lines (Sec. 4.3, 5.1).  Each row accumulates its entries
@@ -18,15 +18,17 @@
 namespace gb {
 namespace {
 
-template <typename T, int R, int U>
+template <typename T, int R, int L, int U>
 __global__ void __launch_bounds__(1024)
 spmv_sell(int32_t n, int32_t n_slices, const int64_t *__restrict__ sp,
           const int32_t *__restrict__ col, const T *__restrict__ val, const T *__restrict__ x,
           T *__restrict__ y) {
-    const int64_t slice = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
+    // L lanes per slice, R rows per lane: S = L R rows per slice
+    constexpr int S = L * R;
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t slice = gt / L;
+    const int lane = (int)(gt % L);
     if (slice >= n_slices) return;
-    constexpr int S = 32 * R;
     const int64_t base = sp[slice];
     const int w = (int)((sp[slice + 1] - base) / S);
     const T *vp = val + base + lane * R;
@@ -137,33 +139,37 @@ inline unsigned grid_for(int64_t threads, int block) {
     return (unsigned)(b < 1 ? 1 : b);
 }
 
+// (R, L) per slice height: FP64 lanes read 8R bytes of values (16 B at S = 64, 32 B at
+// S >= 128); FP32 lanes read 16 B (R = 4) or 32 B (R = 8).
+template <typename T, int R, int L, int U>
+spmv_status_t go_sell(spmv_matrix_t A, const T *val, const T *x, T *y, cudaStream_t st) {
+    const int block = A->block;
+    const unsigned grid = grid_for((int64_t)A->n_slices * L, block);
+    spmv_sell<T, R, L, U><<<grid, block, 0, st>>>(A->n, A->n_slices, A->slice_ptr.p,
+                                                  A->sell_col.p, val, x, y);
+    GB_LAUNCHED();
+    return SPMV_OK;
+}
+
 template <typename T>
 spmv_status_t launch_sell(spmv_matrix_t A, const T *val, const T *x, T *y, cudaStream_t st) {
     if (A->n == 0) return SPMV_OK;
-    const int block = A->block;
-    const unsigned grid = grid_for((int64_t)A->n_slices * 32, block);
-    switch (A->S) {
-        case 32:
-            spmv_sell<T, 1, 4><<<grid, block, 0, st>>>(A->n, A->n_slices, A->slice_ptr.p,
-                                                       A->sell_col.p, val, x, y);
-            break;
-        case 64:
-            spmv_sell<T, 2, 4><<<grid, block, 0, st>>>(A->n, A->n_slices, A->slice_ptr.p,
-                                                       A->sell_col.p, val, x, y);
-            break;
-        case 128:
-            spmv_sell<T, 4, 2><<<grid, block, 0, st>>>(A->n, A->n_slices, A->slice_ptr.p,
-                                                       A->sell_col.p, val, x, y);
-            break;
-        case 256:
-            spmv_sell<T, 8, 1><<<grid, block, 0, st>>>(A->n, A->n_slices, A->slice_ptr.p,
-                                                       A->sell_col.p, val, x, y);
-            break;
-        default:
-            return SPMV_ERR_INVALID_ARG;
+    if constexpr (sizeof(T) == 8) {
+        switch (A->S) {
+            case 32: return go_sell<T, 1, 32, 4>(A, val, x, y, st);
+            case 64: return go_sell<T, 2, 32, 4>(A, val, x, y, st);
+            case 128: return go_sell<T, 4, 32, 2>(A, val, x, y, st);
+            case 256: return go_sell<T, 8, 32, 1>(A, val, x, y, st);
+        }
+    } else {
+        switch (A->S) {
+            case 32: return go_sell<T, 4, 8, 4>(A, val, x, y, st);
+            case 64: return go_sell<T, 4, 16, 4>(A, val, x, y, st);
+            case 128: return go_sell<T, 4, 32, 4>(A, val, x, y, st);
+            case 256: return go_sell<T, 8, 32, 2>(A, val, x, y, st);
+        }
     }
-    GB_LAUNCHED();
-    return SPMV_OK;
+    return SPMV_ERR_INVALID_ARG;
 }
 
 template <typename T>

@@ -1,0 +1,148 @@
+"""GPU CG solves (FP64 Jacobi-PCG, graph-launched and persistent; FP32/FP64 iterative
+refinement) through the C ABI, checked against the CPU oracle.
+
+Bars: the true FP64 residual ||b - A x|| / ||b|| recomputed by the oracle SpMV meets the
+requested tolerance; FP64 iteration counts agree with the oracle's within 2; the persistent
+kernel reproduces the graph-launched path bit for bit; statuses for caps, timeouts and bad
+inputs.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2107_12371_gb300 import capi, meshgen, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    capi.load()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def true_relres(oracle, m, x, b):
+    r = b - oracle.spmv(m.row_ptr, m.col_idx, m.values, x)
+    return np.linalg.norm(r) / np.linalg.norm(b)
+
+
+def solve(A, b, **opts):
+    bd = dev(b)
+    xd = torch.zeros_like(bd)
+    res = A.solve(bd, xd, raise_on_error=False, **opts)
+    torch.cuda.synchronize()
+    return xd.cpu().numpy(), res
+
+
+@pytest.mark.parametrize("n", [3, 8, 14])
+def test_fp64_pcg_matches_oracle(oracle, n):
+    m, b = workloads.kuhn(n, seed=n, dirichlet=True)
+    A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values)
+    x, res = solve(A, b, rtol=1e-10)
+    assert res["status"] == capi.SPMV_OK
+    xo, info = oracle.jacobi_pcg(m.row_ptr, m.col_idx, m.values, b, rtol=1e-10)
+    assert abs(res["iterations"] - info["iterations"]) <= 2
+    assert true_relres(oracle, m, x, b) <= 1e-10
+    assert abs(res["rel_residual"] - true_relres(oracle, m, x, b)) <= 1e-12
+    assert np.linalg.norm(x - xo) <= 1e-7 * np.linalg.norm(xo)
+
+
+def test_persistent_equals_graph_path(oracle):
+    m, b = workloads.kuhn(12, seed=4, dirichlet=True)
+    A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values)
+    x1, r1 = solve(A, b, rtol=1e-10)
+    x2, r2 = solve(A, b, rtol=1e-10, persistent=1)
+    assert r1["status"] == r2["status"] == capi.SPMV_OK
+    assert r1["iterations"] == r2["iterations"]
+    assert np.array_equal(x1, x2)
+    # repeated solves are deterministic
+    x3, r3 = solve(A, b, rtol=1e-10)
+    assert np.array_equal(x1, x3)
+
+
+@pytest.mark.parametrize("reorder", [capi.SPMV_REORDER_NONE, capi.SPMV_REORDER_RCM])
+def test_mixed_refinement_reaches_fp64_residual(oracle, reorder):
+    m, b = workloads.kuhn(12, seed=1, dirichlet=True)
+    A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values, reorder=reorder,
+                    precision=capi.SPMV_PREC_DUAL)
+    bi = torch.empty_like(dev(b))
+    A.permute(0, dev(b), bi)
+    xi = torch.zeros_like(bi)
+    res = A.solve(bi, xi, raise_on_error=False, mixed=1, rtol=1e-10, inner_rtol=1e-4)
+    assert res["status"] == capi.SPMV_OK
+    assert res["outer_iterations"] >= 2
+    x = torch.empty_like(xi)
+    A.permute(1, xi, x)
+    x = x.cpu().numpy()
+    assert true_relres(oracle, m, x, b) <= 1e-10
+    xo, _ = oracle.mixed_ir(m.row_ptr, m.col_idx, m.values, b, rtol=1e-10)
+    x64, _ = oracle.jacobi_pcg(m.row_ptr, m.col_idx, m.values, b, rtol=1e-12)
+    # error against the FP64 solution, within the conditioning of the tolerance
+    assert np.linalg.norm(x - x64) <= 1e-6 * np.linalg.norm(x64)
+    assert np.linalg.norm(xo - x64) <= 1e-6 * np.linalg.norm(x64)
+
+
+def test_start_from_solution_and_zero_rhs(oracle):
+    m, b = workloads.kuhn(6, seed=2, dirichlet=True)
+    A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values)
+    x, res = solve(A, b, rtol=1e-10)
+    xd = dev(x)
+    res2 = A.solve(dev(b), xd, raise_on_error=False, rtol=1e-8, use_x0=1)
+    assert res2["status"] == capi.SPMV_OK and res2["iterations"] == 0
+    z, res3 = solve(A, np.zeros(m.n))
+    assert res3["status"] == capi.SPMV_OK and res3["iterations"] == 0 and not z.any()
+
+
+def test_iteration_cap_and_timeouts():
+    m, b = workloads.kuhn(10, seed=3, dirichlet=True)
+    A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values, precision=capi.SPMV_PREC_DUAL)
+    _, res = solve(A, b, rtol=1e-12, max_iter=5, check_every=2)
+    assert res["status"] == capi.SPMV_ERR_NOT_CONVERGED and res["iterations"] == 5
+    _, res = solve(A, b, rtol=1e-12, max_iter=5, persistent=1)
+    assert res["status"] == capi.SPMV_ERR_NOT_CONVERGED and res["iterations"] == 5
+    # a wall-clock budget that has already expired: the graph path stops after one batch,
+    # the persistent kernel stops at its first budget vote; both report TIMEOUT
+    _, res = solve(A, b, rtol=1e-14, timeout_s=1e-9, check_every=4)
+    assert res["status"] == capi.SPMV_ERR_TIMEOUT
+    _, res = solve(A, b, rtol=1e-14, timeout_s=1e-9, persistent=1)
+    assert res["status"] == capi.SPMV_ERR_TIMEOUT
+    _, res = solve(A, b, rtol=1e-14, timeout_s=1e-9, mixed=1)
+    assert res["status"] == capi.SPMV_ERR_TIMEOUT
+
+
+def test_bad_inputs():
+    # a row without a diagonal entry cannot be Jacobi-preconditioned
+    rp = np.array([0, 1, 2], np.int32)
+    ci = np.array([1, 0], np.int32)
+    A = capi.Matrix(2, rp, ci, np.ones(2))
+    _, res = solve(A, np.ones(2))
+    assert res["status"] == capi.SPMV_ERR_INVALID_CSR
+    m, b = workloads.kuhn(3, seed=0, dirichlet=True)
+    F = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values)
+    _, res = solve(F, b, mixed=1)  # FP64-only handle has no FP32 values
+    assert res["status"] == capi.SPMV_ERR_UNSUPPORTED
+    _, res = solve(F, b, inner_rtol=2.0)
+    assert res["status"] == capi.SPMV_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("mixed", [0, 1])
+def test_c2_full_size_solve(oracle, mixed):
+    """6M-cell Dirichlet mesh in RCM order: the true FP64 residual reaches 1e-10."""
+    m, b = workloads.c2()
+    A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values, reorder=capi.SPMV_REORDER_RCM,
+                    precision=capi.SPMV_PREC_DUAL)
+    bd = dev(b)
+    bi = torch.empty_like(bd)
+    A.permute(0, bd, bi)
+    xi = torch.zeros_like(bi)
+    res = A.solve(bi, xi, raise_on_error=False, rtol=1e-10, mixed=mixed)
+    assert res["status"] == capi.SPMV_OK
+    x = torch.empty_like(xi)
+    A.permute(1, xi, x)
+    assert true_relres(oracle, m, x.cpu().numpy(), b) <= 1e-10
