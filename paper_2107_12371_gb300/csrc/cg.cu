@@ -210,6 +210,8 @@ __global__ void set_scalars(CgScalars *sc, double tol2, int max_iter) {
     sc->iters = 0;
     sc->done = 0;
     for (int k = 0; k < 4; ++k) sc->tickets[k] = 0u;
+    sc->bar_count = 0u;
+    sc->budget_ns = 0;
 }
 
 __global__ void add_iters(CgScalars *inner, int *total) { *total += inner->iters; }
@@ -228,6 +230,7 @@ spmv_status_t ensure_cg_work(spmv_matrix_t A, bool mixed, cudaStream_t st) {
         w.part_len = G;
         GB_TRY(w.part.alloc((size_t)G * kMaxParts * 2, t));
         GB_TRY(w.scal.alloc(2 * ((sizeof(CgScalars) + 7) / 8), t));
+        GB_CUDA(cudaMemsetAsync(w.scal.p, 0, w.scal.n * sizeof(double), st));
         GB_TRY(w.flags.alloc(16, t));
         GB_CUDA(cudaMallocHost((void **)&w.h_scal, 2 * sizeof(CgScalars)));
         GB_CUDA(cudaMallocHost((void **)&w.h_flags, 16 * sizeof(int)));
@@ -553,10 +556,11 @@ spmv_status_t cg_solve(spmv_matrix_t A, const double *b, double *x, const cg_opt
     spmv_status_t s = ensure_cg_work(A, o.mixed != 0, st);
     if (s != SPMV_OK) return (res->status = s);
     CgWork &w = A->cg;
-    if (o.use_x0) {
+    if (o.use_x0)
         s = cuda_status(cudaMemcpyAsync(w.x.p, x, sizeof(double) * A->n, cudaMemcpyDeviceToDevice, st));
-        if (s != SPMV_OK) return (res->status = s);
-    }
+    else
+        s = cuda_status(cudaMemsetAsync(w.x.p, 0, sizeof(double) * A->n, st));
+    if (s != SPMV_OK) return (res->status = s);
     s = o.mixed ? solve_mixed(A, b, o, res, st, t0) : solve64(A, b, o, res, st, t0);
     if (s != SPMV_OK) return (res->status = s);
     double rel = 0.0;

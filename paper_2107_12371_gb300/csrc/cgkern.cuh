@@ -86,8 +86,9 @@ __device__ bool grid_sum_last(double (&v)[NV], double *part, unsigned *ticket, d
 }
 
 // y-rows (R of them) of lane `lane` in slice `slice`: sum over the slice's columns in order,
-// fused multiply-add from +0.0, padding skipped (the same order as spmv_sell).
-template <typename T, int R, int L>
+// fused multiply-add from +0.0, padding skipped (the same order as spmv_sell).  COHERENT
+// selects coherent gathers of x, for kernels in which other CTAs rewrite x between barriers.
+template <typename T, int R, int L, bool COHERENT = false>
 __device__ __forceinline__ void slice_rows(int64_t slice, int lane, const int64_t *sp,
                                            const int32_t *col, const T *val, const T *x,
                                            uint64_t pol, T (&acc)[R]) {
@@ -110,7 +111,9 @@ __device__ __forceinline__ void slice_rows(int64_t slice, int lane, const int64_
 #pragma unroll
         for (int u = 0; u < 2; ++u)
 #pragma unroll
-            for (int i = 0; i < R; ++i) xv[u][i] = c[u][i] >= 0 ? ld_x(x + c[u][i]) : T(0);
+            for (int i = 0; i < R; ++i)
+                xv[u][i] = c[u][i] >= 0 ? (COHERENT ? ld_x_coherent(x + c[u][i]) : ld_x(x + c[u][i]))
+                                        : T(0);
 #pragma unroll
         for (int u = 0; u < 2; ++u)
 #pragma unroll
@@ -124,7 +127,8 @@ __device__ __forceinline__ void slice_rows(int64_t slice, int lane, const int64_
         ld_stream(cp + (int64_t)t * S, pol, c);
 #pragma unroll
         for (int i = 0; i < R; ++i)
-            if (c[i] >= 0) acc[i] = fma_t(v[i], ld_x(x + c[i]), acc[i]);
+            if (c[i] >= 0)
+                acc[i] = fma_t(v[i], COHERENT ? ld_x_coherent(x + c[i]) : ld_x(x + c[i]), acc[i]);
     }
 }
 

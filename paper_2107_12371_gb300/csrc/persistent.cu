@@ -7,7 +7,8 @@
 // decisions.  The results equal the graph-launched path's (same per-CTA partitions, same
 // reduction trees).  Every barrier wait is bounded: after 2 s without progress the waiting
 // CTA records done = 4 (timeout) and the whole grid leaves the loop, so a fault can never
-// leave the GPU spinning.
+// leave the GPU spinning.  p, q, r and x change while the kernel runs, so they are read with
+// coherent loads only (never through the read-only .nc path).
 #include "cgkern.cuh"
 
 namespace gb {
@@ -99,7 +100,7 @@ cg_persistent(int32_t n, int32_t n_slices, const int64_t *sp, const int32_t *col
             const int64_t slice = g / L;
             const int lane = (int)(g % L);
             double acc[R];
-            slice_rows<double, R, L>(slice, lane, sp, col, val, p, pol, acc);
+            slice_rows<double, R, L, true>(slice, lane, sp, col, val, p, pol, acc);
             const int64_t row0 = slice * S + (int64_t)lane * R;
             store_rows<double, R>(q, row0, n, acc);
 #pragma unroll

@@ -94,8 +94,23 @@ __device__ __forceinline__ void ld_stream(const int32_t *p, uint64_t, int32_t (&
 }
 
 // ---- gathers of the multiplying vector (read-only path, L1 allocating) ----------------
+// Only for vectors that no thread writes while the kernel runs.
 __device__ __forceinline__ double ld_x(const double *p) { return __ldg(p); }
 __device__ __forceinline__ float ld_x(const float *p) { return __ldg(p); }
+
+// Coherent gathers (weak ld.global, L1 allocating) for vectors that other CTAs rewrite during
+// the same kernel, between grid barriers whose fences order the writes before these loads
+// (the read-only .nc path above would be allowed to return stale data there).
+__device__ __forceinline__ double ld_x_coherent(const double *p) {
+    double v;
+    asm volatile("ld.global.ca.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ float ld_x_coherent(const float *p) {
+    float v;
+    asm volatile("ld.global.ca.f32 %0, [%1];" : "=f"(v) : "l"(p) : "memory");
+    return v;
+}
 
 // ---- stores of R consecutive results -----------------------------------------------------
 template <typename T, int R>
