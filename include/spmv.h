@@ -195,6 +195,37 @@ spmv_status_t cg_default_options(cg_options_t *opt);
 spmv_status_t cg_solve(spmv_matrix_t A, const double *b_dev, double *x_dev, const cg_options_t *opt,
                        cg_result_t *result, void *stream);
 
+/* ------------------------------ allocation-free solve ----------------------------------- */
+/* Largest system (rows) that cg_solve_csr_noalloc accepts. */
+#define SPMV_NOALLOC_MAX_ROWS 65536
+
+/*
+ * cg_solve_csr_noalloc -- sync.  The paper has no counterpart to this entry point.  It is for
+ * callers that cannot allocate device memory when they solve, and therefore cannot create a
+ * matrix handle (spmv_create allocates): for example a plugin inside a host application that
+ * owns and pools all GPU memory itself, or a real-time loop whose memory is fixed in advance.
+ * It solves A x = b by FP64 Jacobi-preconditioned CG (the iteration of cg_solve, with a
+ * thread-per-row CSR product) directly on caller-owned device CSR arrays, and calls no
+ * cudaMalloc, cudaFree or other allocating routine.  Its work vectors and reduction scratch
+ * live in one fixed array inside the library (4 * SPMV_NOALLOC_MAX_ROWS doubles plus about
+ * 33 KB of partial sums and scalars, about 2.1 MB), which every GPU that loads the library
+ * holds until the process exits.
+ *   n <= SPMV_NOALLOC_MAX_ROWS, else SPMV_ERR_INVALID_ARG with no device work.  row_ptr_dev,
+ *   col_idx_dev, values_dev: device CSR with the layout and checks of spmv_create (checked on
+ *   the device: SPMV_ERR_INVALID_CSR; a zero or missing diagonal is also INVALID_CSR).
+ *   b_dev, x_dev: device double[n]; x_dev holds x0 when opt->use_x0, else it is overwritten
+ *   starting from 0.  opt->mixed and opt->persistent give SPMV_ERR_UNSUPPORTED.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  All calls share the
+ * one array, which keeps the last call's contents; each call clears what it needs at its
+ * start.  Calls that overlap on the GPU (other streams, other host threads) race on the array
+ * and must be serialised by the caller.
+ */
+spmv_status_t cg_solve_csr_noalloc(int32_t n, int64_t nnz, const int32_t *row_ptr_dev,
+                                   const int32_t *col_idx_dev, const double *values_dev,
+                                   const double *b_dev, double *x_dev, const cg_options_t *opt,
+                                   cg_result_t *result, void *stream);
+
 /* ------------------------------ continuous-batching server ------------------------------ */
 typedef struct {
     uint64_t submitted, completed, rejected;

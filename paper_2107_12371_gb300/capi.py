@@ -99,6 +99,8 @@ _SIGS = {
     "spmv_permute": [_P, _int, _int, _P, _P, _P],
     "cg_default_options": [ctypes.POINTER(cg_options_t)],
     "cg_solve": [_P, _P, _P, ctypes.POINTER(cg_options_t), ctypes.POINTER(cg_result_t), _P],
+    "cg_solve_csr_noalloc": [_i32, _i64, _P, _P, _P, _P, _P, ctypes.POINTER(cg_options_t),
+                             ctypes.POINTER(cg_result_t), _P],
     "spmv_server_create": [ctypes.c_size_t, _int, ctypes.POINTER(_P)],
     "spmv_server_submit": [_P, _i32, _i64, _P, _P, _P, _P, ctypes.POINTER(cg_options_t),
                            ctypes.POINTER(ctypes.c_uint64)],
@@ -275,6 +277,21 @@ def cg_solve(h, b, x, options=None, stream=None, raise_on_error=True):
     if raise_on_error and st not in (SPMV_OK,):
         raise SpmvError(st, "cg_solve")
     return out
+
+
+SPMV_NOALLOC_MAX_ROWS = 65536
+
+
+def cg_solve_csr_noalloc(n, row_ptr, col_idx, values, b, x, options=None, stream=None):
+    """Allocation-free CG on device CSR tensors; returns the result dict (status included)."""
+    opt = options if options is not None else cg_default_options()
+    res = cg_result_t()
+    nnz = int(col_idx.numel()) if col_idx is not None else 0
+    st = load().cg_solve_csr_noalloc(int(n), nnz, _ptr(row_ptr), _ptr(col_idx), _ptr(values),
+                                     _ptr(b), _ptr(x), ctypes.byref(opt), ctypes.byref(res),
+                                     _stream(stream))
+    return dict(iterations=res.iterations, outer_iterations=res.outer_iterations,
+                rel_residual=res.rel_residual, status=st)
 
 
 def spmv_server_create(budget_bytes, max_slots):
