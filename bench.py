@@ -3,7 +3,7 @@
 
 Workload (one step): y = A x, FP64, on the Kuhn-tet 100^3 cube (6,000,000 cells,
 29,880,000 non-zeros, Dirichlet, cells randomly permuted then RCM-reordered), inputs resident
-in HBM, L2 flushed (256 MB write) between timed steps.  The metric is effective bandwidth:
+in HBM, L2 flushed (256 MB written, then 256 MB read) between timed steps.  The metric is effective bandwidth:
 algorithmic bytes 12 nnz + 16 N (each value, index, x and y entry once) per step / time.
 
 Secondary results measured once after the timed loop (same JSON line): FP32 product of the same
@@ -33,7 +33,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "SpMV effective GB/s (% HBM peak) FP64 vs mixed; served CG solves/s, p99"
 WORKLOAD = "kuhn-tet 100^3 FV Laplacian, Dirichlet, 6,000,000 rows, 29,880,000 nnz, RCM order"
-FLUSH_BYTES = 256 << 20
+FLUSH_BYTES = 512 << 20  # 256 MB written + 256 MB read between timed steps
 
 
 def spmv_bytes(n, nnz, f32=False):
@@ -192,13 +192,21 @@ def cpu_baseline(rp, ci, v, x, nbytes, budget_s=10.0):
                       "(%.1f s, single thread)" % (reps, dt)}
 
 
+def flush_l2(flush_buf):
+    """Write a buffer larger than L2 (evicts every line of the previous step), then read a
+    second one, so the dirty lines of the write are written back before the timed kernel."""
+    half = flush_buf.numel() // 2
+    flush_buf[:half].add_(1)
+    return flush_buf[half:].sum()
+
+
 def time_kernel(torch, fn, steps, flush_buf, stream):
     """Per-step CUDA-event times (ms) of fn() with an L2 flush before each step."""
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(steps)]
     with torch.cuda.stream(stream):
         for a, b in evs:
-            flush_buf.add_(1)
+            flush_l2(flush_buf)
             a.record(stream)
             fn()
             b.record(stream)
@@ -269,6 +277,14 @@ def run_gpu(args):
     peak, peak_src = measured_peaks()
 
     if args.profile:
+        if args.profile_cg > 0:
+            # a few CG iterations of both solvers, for launch lists of the CG kernels
+            bi = xi.clone()
+            for mixed in (0, 1):
+                xs = torch.zeros_like(bi)
+                A.solve(bi, xs, stream, raise_on_error=False, rtol=1e-10, mixed=mixed,
+                        max_iter=args.profile_cg, max_outer=2)
+            torch.cuda.synchronize(dev)
         if rank == 0:
             print(json.dumps({"profile_run": True, "value": value, "unit": "GB/s"}), flush=True)
         return 0
@@ -311,7 +327,7 @@ def run_gpu(args):
         "config": {"workload": WORKLOAD, "n": n, "nnz": nnz, "format": "sliced ELLPACK",
                    "slice_height": info["slice_height"], "reorder": "rcm",
                    "bandwidth": info["bandwidth"], "max_slice_span": info["max_slice_span"],
-                   "algorithmic_bytes_per_step": nbytes, "l2": "flushed (256 MB write) between steps",
+                   "algorithmic_bytes_per_step": nbytes, "l2": "flushed between steps (256 MB write, then 256 MB read)",
                    "create_s": round(t_create, 3), "wall_s_timed_region": round(wall, 4),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "pct_hbm_peak": 100.0 * (value / world) / peak,
@@ -326,6 +342,8 @@ def run_gpu(args):
                      "traffic": traffic_from_profile("spmv_sell_f64_c2_rcm")},
     }
     line.update(extra)
+    if rank == 0 and not args.quick and args.serve_requests > 0:
+        line.update(serving_results(args, capi, torch))
     if not args.no_cpu_baseline:
         rp, ci, v = capi.spmv_export_csr(A.handle, n, nnz)
         line["cpu_baseline"] = cpu_baseline(rp, ci, v, xi.cpu().numpy(), nbytes)
@@ -404,6 +422,81 @@ def cg_results(torch, capi, m, b, A, bi, dev):
     return out
 
 
+def _make_request(args):
+    index, cells = args
+    from paper_2107_12371_gb300 import workloads
+    m, b = workloads.serving_request(index, cells)
+    return index, m.n, m.row_ptr, m.col_idx, m.values, b
+
+
+def serving_results(args, capi, torch):
+    """A bounded sample of the serving stream: the first n requests of the 2,000-request
+    stream (cell counts log-uniform in [1e4, 2e6], seed = request index, FP64 or mixed
+    precision by a seeded coin, rtol 1e-8), solved (a) one at a time through cg_solve and (b)
+    through the server with Poisson arrivals at twice the one-at-a-time rate, 60 GB budget."""
+    import multiprocessing as mp
+    from paper_2107_12371_gb300 import workloads
+    n_req = args.serve_requests
+    sizes = workloads.serving_sizes(2000, seed=0)[:n_req]
+    coin = np.random.default_rng(1).random(2000)[:n_req] < 0.5
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        reqs = sorted(pool.map(_make_request, list(enumerate(sizes))), key=lambda r: r[0])
+    opts = [capi.cg_default_options(rtol=1e-8, mixed=int(c)) for c in coin]
+    cells = [r[1] for r in reqs]
+    # (a) one at a time
+    lat_serial = []
+    t_all = time.perf_counter()
+    for (i, n, rp, ci, v, b), o in zip(reqs, opts):
+        t0 = time.perf_counter()
+        A = capi.Matrix(n, rp, ci, v, precision=capi.SPMV_PREC_DUAL if o.mixed else 0)
+        bd = torch.from_numpy(b).cuda()
+        xd = torch.zeros_like(bd)
+        A.solve(bd, xd, raise_on_error=False, **{f: getattr(o, f) for f, _ in o._fields_})
+        xd.cpu()
+        A.close()
+        lat_serial.append(time.perf_counter() - t0)
+    t_serial = time.perf_counter() - t_all
+    rate_serial = n_req / t_serial
+    # (b) served, Poisson arrivals at twice the serial rate
+    lam = 2.0 * rate_serial
+    gaps = np.random.default_rng(2).exponential(1.0 / lam, size=n_req)
+    srv = capi.spmv_server_create(60 << 30, args.serve_slots)
+    tickets = []
+    pending = {}
+    t0 = time.perf_counter()
+    next_t = t0
+    results = {}
+    for (i, n, rp, ci, v, b), o, g in zip(reqs, opts, gaps):
+        next_t += g
+        while time.perf_counter() < next_t:
+            time.sleep(0.0002)
+        t = capi.spmv_server_submit(srv, n, rp, ci, v, b, o)
+        tickets.append(t)
+        pending[t] = n
+    while pending:
+        for t in list(pending):
+            r = capi.spmv_server_poll(srv, t, np.empty(pending[t]))
+            if r is not None:
+                results[t] = r
+                del pending[t]
+        time.sleep(0.0005)
+    t_served = time.perf_counter() - t0
+    st = capi.spmv_server_get_stats(srv)
+    capi.spmv_server_destroy(srv)
+    ok = sum(1 for r in results.values() if r["status"] == capi.SPMV_OK)
+    worst = max(r["rel_residual"] for r in results.values())
+    return {"serving": {
+        "sample": "requests 0..%d of the 2,000-request stream (%d..%d cells, mean %d)" % (
+            n_req - 1, min(cells), max(cells), int(np.mean(cells))),
+        "slots": args.serve_slots, "budget_bytes": 60 << 30, "arrival_rate_per_s": lam,
+        "solves_per_s": n_req / t_served, "p50_latency_s": st["p50_latency_s"],
+        "p99_latency_s": st["p99_latency_s"], "peak_bytes": st["peak_bytes"],
+        "converged": ok, "max_rel_residual": worst,
+        "one_at_a_time": {"solves_per_s": rate_serial,
+                          "p50_latency_s": float(np.percentile(lat_serial, 50)),
+                          "p99_latency_s": float(np.percentile(lat_serial, 99))}}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -413,6 +506,10 @@ def main():
     ap.add_argument("--slice-height", type=int, default=64)
     ap.add_argument("--quick", action="store_true", help="headline only, no secondary results")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-cg", type=int, default=0,
+                    help="with --profile: also run CG solves capped at this many iterations")
+    ap.add_argument("--serve-requests", type=int, default=48)
+    ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--profile", action="store_true",
                     help="timed SpMV loop only (for ncu launch lists and captures)")
     args = ap.parse_args()

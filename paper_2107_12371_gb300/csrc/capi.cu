@@ -9,6 +9,11 @@
 
 namespace gb {
 
+cudaStream_t &alloc_stream() {
+    static thread_local cudaStream_t s = nullptr;
+    return s;
+}
+
 const DeviceFacts &device_facts() {
     static DeviceFacts facts[64];
     static std::mutex mu;
@@ -101,6 +106,8 @@ spmv_status_t spmv_create(int32_t n_rows, int32_t n_cols, int64_t nnz, const int
 
     spmv_matrix_t A = new (std::nothrow) spmv_matrix_s();
     if (!A) return SPMV_ERR_OOM;
+    AllocStream alloc_scope(st);
+    A->stream = st;
     A->n = n_rows;
     A->nnz = nnz;
     A->opt = o;
@@ -151,8 +158,13 @@ spmv_status_t spmv_create(int32_t n_rows, int32_t n_cols, int64_t nnz, const int
 
 spmv_status_t spmv_destroy(spmv_matrix_t A) {
     if (!A) return SPMV_OK;
+    // the creation stream may no longer exist: free on the legacy stream after a device sync
     cudaDeviceSynchronize();
-    release_matrix(A);
+    {
+        AllocStream alloc_scope(nullptr);
+        release_matrix(A);
+    }
+    cudaDeviceSynchronize();
     return SPMV_OK;
 }
 

@@ -131,17 +131,8 @@ __global__ void __launch_bounds__(kCgBlock)
 cg_update_xr(int32_t n, T *x, T *r, const T *p, const T *q, const T *dinv, double *part,
              CgScalars *sc) {
     if (sc->done) return;
-    const T alpha = (T)sc->alpha;
     T vz = T(0), vr = T(0);
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const T xi = fma_t(alpha, p[i], x[i]);
-        const T ri = fma_t(-alpha, q[i], r[i]);
-        x[i] = xi;
-        r[i] = ri;
-        vz = fma_t(ri, dinv[i] * ri, vz);
-        vr = fma_t(ri, ri, vr);
-    }
+    sweep_update_xr<T>(n, (T)sc->alpha, x, r, p, q, dinv, vz, vr);
     double v[2] = {(double)vz, (double)vr};
     double tot[2];
     if (grid_sum_last<2>(v, part, &sc->tickets[2], tot) && threadIdx.x == 0) {
@@ -161,10 +152,7 @@ template <typename T>
 __global__ void __launch_bounds__(kCgBlock)
 cg_update_p(int32_t n, const T *r, const T *dinv, T *p, const CgScalars *sc) {
     if (sc->done) return;
-    const T beta = (T)sc->beta;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-        p[i] = fma_t(beta, p[i], dinv[i] * r[i]);
+    sweep_update_p<T>(n, (T)sc->beta, r, dinv, p);
 }
 
 // refinement: right-hand side of the inner solve r32 = fp32(r64 / ||r64||), start of the
@@ -218,8 +206,9 @@ __global__ void add_iters(CgScalars *inner, int *total) { *total += inner->iters
 
 }  // namespace
 
-// grid of the CG sweeps: a fixed multiple of the SM count, so the reduction order is fixed
-static int cg_grid() { return device_facts().sm_count * 4; }
+// grid of the CG sweeps: a fixed multiple of the SM count (the persistent kernel uses the
+// same grid), so the reduction order is fixed and both paths give identical results
+int cg_grid() { return device_facts().sm_count * kCgCtasPerSm; }
 
 spmv_status_t ensure_cg_work(spmv_matrix_t A, bool mixed, cudaStream_t st) {
     CgWork &w = A->cg;
@@ -232,8 +221,6 @@ spmv_status_t ensure_cg_work(spmv_matrix_t A, bool mixed, cudaStream_t st) {
         GB_TRY(w.scal.alloc(2 * ((sizeof(CgScalars) + 7) / 8), t));
         GB_CUDA(cudaMemsetAsync(w.scal.p, 0, w.scal.n * sizeof(double), st));
         GB_TRY(w.flags.alloc(16, t));
-        GB_CUDA(cudaMallocHost((void **)&w.h_scal, 2 * sizeof(CgScalars)));
-        GB_CUDA(cudaMallocHost((void **)&w.h_flags, 16 * sizeof(int)));
         GB_TRY(w.x.alloc(n, t));
         GB_TRY(w.r.alloc(n, t));
         GB_TRY(w.p.alloc(n, t));
@@ -363,8 +350,8 @@ static spmv_status_t read_scalars(spmv_matrix_t A, cudaStream_t st, CgScalars *o
     CgWork &w = A->cg;
     GB_CUDA(cudaMemcpyAsync(w.h_scal, w.scal.p, 2 * sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
     GB_CUDA(cudaStreamSynchronize(st));
-    if (outer) *outer = ((CgScalars *)w.h_scal)[0];
-    if (inner) *inner = ((CgScalars *)w.h_scal)[1];
+    if (outer) *outer = w.h_scal[0];
+    if (inner) *inner = w.h_scal[1];
     return SPMV_OK;
 }
 
@@ -503,8 +490,6 @@ void release_cg(spmv_matrix_t A) {
     w.x.release(t); w.r.release(t); w.p.release(t); w.q.release(t); w.dinv.release(t);
     w.r32.release(t); w.p32.release(t); w.q32.release(t); w.d32.release(t); w.dinv32.release(t);
     w.part.release(t); w.scal.release(t); w.flags.release(t);
-    if (w.h_flags) cudaFreeHost(w.h_flags);
-    if (w.h_scal) cudaFreeHost(w.h_scal);
     if (w.graph64) cudaGraphExecDestroy(w.graph64);
     if (w.graph32) cudaGraphExecDestroy(w.graph32);
     if (w.cap_stream) cudaStreamDestroy(w.cap_stream);
@@ -552,6 +537,7 @@ spmv_status_t cg_solve(spmv_matrix_t A, const double *b, double *x, const cg_opt
         return SPMV_OK;
     }
     cudaStream_t st = (cudaStream_t)stream;
+    AllocStream alloc_scope(st);
     const auto t0 = Clock::now();
     spmv_status_t s = ensure_cg_work(A, o.mixed != 0, st);
     if (s != SPMV_OK) return (res->status = s);

@@ -10,6 +10,9 @@
 namespace gb {
 
 constexpr int kCgBlock = 256;
+constexpr int kCgCtasPerSm = 4;  // CTAs per SM of every CG sweep (graph and persistent)
+
+int cg_grid();
 
 // Sum over the CTA in a fixed tree; the total is left in every lane of warp 0.
 template <int NV>
@@ -130,6 +133,109 @@ __device__ __forceinline__ void slice_rows(int64_t slice, int lane, const int64_
             if (c[i] >= 0)
                 acc[i] = fma_t(v[i], COHERENT ? ld_x_coherent(x + c[i]) : ld_x(x + c[i]), acc[i]);
     }
+}
+
+// ---- vector sweeps of one CG iteration (grid-stride, 16-byte vectors, scalar tail) --------
+// Shared by the graph-launched kernels and the persistent kernel, so both produce the same
+// per-thread partial sums.  Vectors are plain (coherent) loads: inside the persistent kernel
+// they are rewritten between grid barriers.
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<double> {
+    using type = double2;
+    static constexpr int n = 2;
+};
+template <>
+struct Vec16<float> {
+    using type = float4;
+    static constexpr int n = 4;
+};
+
+template <typename T>
+__device__ __forceinline__ void vload(const T *p, T (&v)[Vec16<T>::n]) {
+    const typename Vec16<T>::type t = *reinterpret_cast<const typename Vec16<T>::type *>(p);
+    if constexpr (Vec16<T>::n == 2) {
+        v[0] = t.x;
+        v[1] = t.y;
+    } else {
+        v[0] = t.x;
+        v[1] = t.y;
+        v[2] = t.z;
+        v[3] = t.w;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void vstore(T *p, const T (&v)[Vec16<T>::n]) {
+    typename Vec16<T>::type t;
+    if constexpr (Vec16<T>::n == 2) {
+        t.x = v[0];
+        t.y = v[1];
+    } else {
+        t.x = v[0];
+        t.y = v[1];
+        t.z = v[2];
+        t.w = v[3];
+    }
+    *reinterpret_cast<typename Vec16<T>::type *>(p) = t;
+}
+
+// x += alpha p; r -= alpha q; accumulates r.(D^-1 r) into vz and r.r into vr
+template <typename T>
+__device__ __forceinline__ void sweep_update_xr(int32_t n, T alpha, T *x, T *r, const T *p,
+                                                const T *q, const T *dinv, T &vz, T &vr) {
+    constexpr int V = Vec16<T>::n;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nv = n / V;
+    for (int64_t v = tid; v < nv; v += stride) {
+        const int64_t i = v * V;
+        T xv[V], rv[V], pv[V], qv[V], dv[V];
+        vload(x + i, xv);
+        vload(r + i, rv);
+        vload(p + i, pv);
+        vload(q + i, qv);
+        vload(dinv + i, dv);
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            xv[e] = fma_t(alpha, pv[e], xv[e]);
+            rv[e] = fma_t(-alpha, qv[e], rv[e]);
+            vz = fma_t(rv[e], dv[e] * rv[e], vz);
+            vr = fma_t(rv[e], rv[e], vr);
+        }
+        vstore(x + i, xv);
+        vstore(r + i, rv);
+    }
+    for (int64_t i = nv * V + tid; i < n; i += stride) {
+        const T xi = fma_t(alpha, p[i], x[i]);
+        const T ri = fma_t(-alpha, q[i], r[i]);
+        x[i] = xi;
+        r[i] = ri;
+        vz = fma_t(ri, dinv[i] * ri, vz);
+        vr = fma_t(ri, ri, vr);
+    }
+}
+
+// p = D^-1 r + beta p
+template <typename T>
+__device__ __forceinline__ void sweep_update_p(int32_t n, T beta, const T *r, const T *dinv,
+                                               T *p) {
+    constexpr int V = Vec16<T>::n;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nv = n / V;
+    for (int64_t v = tid; v < nv; v += stride) {
+        const int64_t i = v * V;
+        T rv[V], dv[V], pv[V];
+        vload(r + i, rv);
+        vload(dinv + i, dv);
+        vload(p + i, pv);
+#pragma unroll
+        for (int e = 0; e < V; ++e) pv[e] = fma_t(beta, pv[e], dv[e] * rv[e]);
+        vstore(p + i, pv);
+    }
+    for (int64_t i = nv * V + tid; i < n; i += stride) p[i] = fma_t(beta, p[i], dinv[i] * r[i]);
 }
 
 // (R, L) of the sliced kernels for a slice height and value type.

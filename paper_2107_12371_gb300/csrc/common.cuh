@@ -40,6 +40,16 @@ inline spmv_status_t cuda_status(cudaError_t e) {
 
 #define GB_LAUNCHED() GB_CUDA(cudaGetLastError())
 
+// Stream on which handle buffers are allocated and freed (stream-ordered allocator), set for
+// the duration of an entry point by AllocStream.  Stream-ordered frees never synchronize the
+// whole device, so solves running concurrently on other streams are not stalled.
+cudaStream_t &alloc_stream();
+struct AllocStream {
+    cudaStream_t saved;
+    explicit AllocStream(cudaStream_t s) : saved(alloc_stream()) { alloc_stream() = s; }
+    ~AllocStream() { alloc_stream() = saved; }
+};
+
 // A device allocation owned by the handle.
 template <typename T>
 struct DevBuf {
@@ -48,7 +58,7 @@ struct DevBuf {
     spmv_status_t alloc(size_t count, size_t *tally) {
         release(tally);
         if (count == 0) count = 1;
-        cudaError_t e = cudaMalloc((void **)&p, count * sizeof(T));
+        cudaError_t e = cudaMallocAsync((void **)&p, count * sizeof(T), alloc_stream());
         if (e != cudaSuccess) {
             p = nullptr;
             cudaGetLastError();
@@ -60,7 +70,7 @@ struct DevBuf {
     }
     void release(size_t *tally) {
         if (p) {
-            cudaFree(p);
+            cudaFreeAsync(p, alloc_stream());
             if (tally) *tally -= n * sizeof(T);
         }
         p = nullptr;
@@ -87,8 +97,8 @@ struct CgWork {
     DevBuf<double> part;        // per-CTA partial sums
     DevBuf<double> scal;        // two CgScalars blocks (outer / inner)
     DevBuf<int> flags;          // status flags
-    int *h_flags = nullptr;     // pinned host mirror
-    double *h_scal = nullptr;   // pinned host mirror
+    int h_flags[16] = {};       // host mirrors (read back synchronously; no pinned buffers)
+    CgScalars h_scal[2] = {};
     int part_len = 0;
     bool ready = false;
     bool mixed_ready = false;
@@ -101,6 +111,7 @@ struct CgWork {
 }  // namespace gb
 
 struct spmv_matrix_s {
+    cudaStream_t stream = nullptr;  // creation stream: buffers are allocated / freed on it
     int32_t n = 0;
     int64_t nnz = 0;
     spmv_options_t opt{};

@@ -75,7 +75,7 @@ __device__ void store_parts(double (&v)[NV], double *part) {
 }
 
 template <int R, int L>
-__global__ void __launch_bounds__(kCgBlock)
+__global__ void __launch_bounds__(kCgBlock, kCgCtasPerSm)
 cg_persistent(int32_t n, int32_t n_slices, const int64_t *sp, const int32_t *col,
               const double *val, double *x, double *r, double *p, double *q, const double *dinv,
               double *part, CgScalars *sc) {
@@ -129,14 +129,7 @@ cg_persistent(int32_t n, int32_t n_slices, const int64_t *sp, const int32_t *col
         const double alpha = rho / t1[0];
         // phase 2: x += alpha p, r -= alpha q, r.z, r.r
         double vz = 0.0, vr = 0.0;
-        for (int64_t i = tid; i < n; i += lanes) {
-            const double xi = fma(alpha, p[i], x[i]);
-            const double ri = fma(-alpha, q[i], r[i]);
-            x[i] = xi;
-            r[i] = ri;
-            vz = fma(ri, dinv[i] * ri, vz);
-            vr = fma(ri, ri, vr);
-        }
+        sweep_update_xr<double>(n, alpha, x, r, p, q, dinv, vz, vr);
         double v2[2] = {vz, vr};
         store_parts<2>(v2, part2);
         if (!grid_barrier(sc)) {
@@ -156,7 +149,7 @@ cg_persistent(int32_t n, int32_t n_slices, const int64_t *sp, const int32_t *col
             break;
         }
         // phase 3: p = D^-1 r + beta p
-        for (int64_t i = tid; i < n; i += lanes) p[i] = fma(beta, p[i], dinv[i] * r[i]);
+        sweep_update_p<double>(n, beta, r, dinv, p);
         if (!grid_barrier(sc)) {
             done = 4;
             break;
@@ -183,9 +176,9 @@ spmv_status_t cg_persistent64(spmv_matrix_t A, const cg_options_t &o, CgScalars 
         if (w.pers_grid == 0) {
             int per_sm = 0;
             GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCgBlock, 0));
-            if (per_sm < 1) return SPMV_ERR_UNSUPPORTED;
-            const int G = device_facts().sm_count * (per_sm < 4 ? per_sm : 4);
-            w.pers_grid = G < w.part_len ? G : w.part_len;
+            // the grid must be co-resident and equal to the graph path's grid
+            if (per_sm < kCgCtasPerSm) return SPMV_ERR_UNSUPPORTED;
+            w.pers_grid = cg_grid();
         }
         const long long budget = o.timeout_s > 0 ? (long long)(o.timeout_s * 1e9) : 0;
         GB_CUDA(cudaMemcpyAsync(&sc->budget_ns, &budget, sizeof(budget), cudaMemcpyHostToDevice, st));
@@ -200,7 +193,7 @@ spmv_status_t cg_persistent64(spmv_matrix_t A, const cg_options_t &o, CgScalars 
                                             args, 0, st));
         GB_CUDA(cudaMemcpyAsync(w.h_scal, w.scal.p, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
         GB_CUDA(cudaStreamSynchronize(st));
-        *out = *(CgScalars *)w.h_scal;
+        *out = w.h_scal[0];
         return SPMV_OK;
     });
 }

@@ -1,25 +1,291 @@
 // server.cu -- continuous-batching CG solve server.
+//
+// Requests (a CSR system and a right-hand side, copied at submit) wait in a FIFO queue.  A
+// request is admitted as soon as a slot is free and its estimated device footprint fits in
+// what the memory budget has left; its solve then runs on the slot's own CUDA stream, so the
+// kernels of all admitted solves overlap on the GPU while new requests keep arriving.  A slot
+// takes the next request the moment its solve finishes (no batch boundaries).  Each solve
+// keeps its matrix, vectors and CG state in HBM until it completes; only x returns to the
+// host.  Every per-problem kernel uses the same fixed grid and reduction order whatever else
+// runs, so a result is bit-identical alone and in a mix.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
 #include "common.cuh"
+
+namespace gb {
+void release_matrix(spmv_matrix_t A);
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+    uint64_t ticket = 0;
+    int32_t n = 0;
+    int64_t nnz = 0;
+    std::vector<int32_t> rp, ci;
+    std::vector<double> val, b, x;
+    cg_options_t opt{};
+    cg_result_t result{};
+    spmv_status_t status = SPMV_ERR_PENDING;
+    size_t est_bytes = 0;
+    Clock::time_point t_submit, t_start, t_done;
+    bool done = false;
+};
+
+// Conservative device footprint of one solve: CSR copy + sliced ELLPACK (+ FP32 values for
+// mixed precision) + conversion temporaries + CG work vectors + b and x.
+size_t estimate_bytes(int32_t n, int64_t nnz, bool mixed) {
+    const double N = (double)n, Z = (double)nnz;
+    double b = 4.0 * (N + 1) + 12.0 * Z          // CSR copy
+               + 12.0 * Z * 1.1 + 8.0 * N / 32.0   // sliced ELLPACK, padding margin
+               + 4.0 * (N + 1) + 12.0 * Z          // input copies during conversion
+               + 5.0 * 8.0 * N                     // x r p q dinv
+               + 2.0 * 8.0 * N;                    // b, x of the request
+    if (mixed) b += 4.0 * Z + 4.0 * Z * 1.1 + 5.0 * 4.0 * N;
+    return (size_t)b + (4u << 20);
+}
+
+}  // namespace
+}  // namespace gb
+
+struct spmv_server_s {
+    size_t budget = 0;
+    int max_slots = 1;
+    int device = 0;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<gb::Request *> queue;
+    std::unordered_map<uint64_t, gb::Request *> all;
+    size_t bytes_in_use = 0, peak = 0;
+    int active = 0;
+    uint64_t next_ticket = 1, submitted = 0, completed = 0, rejected = 0;
+    std::vector<double> latencies;
+    std::vector<std::thread> workers;
+    bool stop = false;
+};
+
+namespace gb {
+namespace {
+
+// One solve on the slot's stream.  The handle, b and x live on the device only for its
+// duration; they are freed stream-ordered on the slot's stream.
+void run_request(Request *r, cudaStream_t st) {
+    AllocStream scope(st);
+    spmv_options_t o;
+    spmv_default_options(&o);
+    o.precision = r->opt.mixed ? SPMV_PREC_DUAL : SPMV_PREC_FP64;
+    o.reorder = SPMV_REORDER_NONE;
+    spmv_matrix_t A = nullptr;
+    r->status = spmv_create(r->n, r->n, r->nnz, r->rp.data(), r->nnz ? r->ci.data() : nullptr,
+                            r->nnz ? r->val.data() : nullptr, 0, &o, st, &A);
+    if (r->status != SPMV_OK) return;
+    double *d_b = nullptr, *d_x = nullptr;
+    const size_t vb = sizeof(double) * (size_t)(r->n > 0 ? r->n : 1);
+    spmv_status_t s = cuda_status(cudaMallocAsync((void **)&d_b, vb, st));
+    if (s == SPMV_OK) s = cuda_status(cudaMallocAsync((void **)&d_x, vb, st));
+    if (s == SPMV_OK && r->n > 0)
+        s = cuda_status(cudaMemcpyAsync(d_b, r->b.data(), vb, cudaMemcpyHostToDevice, st));
+    if (s == SPMV_OK) {
+        cg_options_t co = r->opt;
+        co.use_x0 = 0;
+        co.persistent = 0;
+        s = cg_solve(A, d_b, d_x, &co, &r->result, st);
+        if (r->n > 0 && (s == SPMV_OK || s == SPMV_ERR_NOT_CONVERGED || s == SPMV_ERR_TIMEOUT)) {
+            r->x.resize((size_t)r->n);
+            spmv_status_t c =
+                cuda_status(cudaMemcpyAsync(r->x.data(), d_x, vb, cudaMemcpyDeviceToHost, st));
+            if (c == SPMV_OK) c = cuda_status(cudaStreamSynchronize(st));
+            if (c != SPMV_OK) s = c;
+        }
+    }
+    r->status = s;
+    cudaStreamSynchronize(st);
+    if (d_b) cudaFreeAsync(d_b, st);
+    if (d_x) cudaFreeAsync(d_x, st);
+    release_matrix(A);
+    cudaStreamSynchronize(st);
+}
+
+void worker(spmv_server_t S) {
+    cudaSetDevice(S->device);
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        st = nullptr;
+    }
+    for (;;) {
+        Request *r = nullptr;
+        {
+            std::unique_lock<std::mutex> lock(S->mu);
+            S->cv.wait(lock, [&] {
+                return S->stop || (!S->queue.empty() &&
+                                   S->bytes_in_use + S->queue.front()->est_bytes <= S->budget);
+            });
+            if (S->stop) break;
+            r = S->queue.front();
+            S->queue.pop_front();
+            S->bytes_in_use += r->est_bytes;
+            S->peak = std::max(S->peak, S->bytes_in_use);
+            S->active += 1;
+        }
+        r->t_start = Clock::now();
+        if (st) run_request(r, st);
+        else r->status = SPMV_ERR_CUDA;
+        r->t_done = Clock::now();
+        {
+            std::lock_guard<std::mutex> lock(S->mu);
+            S->bytes_in_use -= r->est_bytes;
+            S->active -= 1;
+            S->completed += 1;
+            S->latencies.push_back(std::chrono::duration<double>(r->t_done - r->t_submit).count());
+            r->result.status = r->status;
+            r->done = true;
+        }
+        S->cv.notify_all();
+    }
+    if (st) cudaStreamDestroy(st);
+}
+
+double percentile(std::vector<double> v, double q) {
+    if (v.empty()) return 0.0;
+    std::sort(v.begin(), v.end());
+    const double pos = q * (double)(v.size() - 1);
+    const size_t i = (size_t)pos;
+    const double f = pos - (double)i;
+    return i + 1 < v.size() ? v[i] * (1.0 - f) + v[i + 1] * f : v[i];
+}
+
+}  // namespace
+}  // namespace gb
+
+using namespace gb;
 
 extern "C" {
 
-spmv_status_t spmv_server_create(size_t, int, spmv_server_t *out) {
-    if (out) *out = nullptr;
-    return SPMV_ERR_UNSUPPORTED;
+spmv_status_t spmv_server_create(size_t hbm_budget_bytes, int max_slots, spmv_server_t *out) {
+    if (!out) return SPMV_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (hbm_budget_bytes == 0 || max_slots < 1 || max_slots > 256) return SPMV_ERR_INVALID_ARG;
+    spmv_server_t S = new (std::nothrow) spmv_server_s();
+    if (!S) return SPMV_ERR_OOM;
+    S->budget = hbm_budget_bytes;
+    S->max_slots = max_slots;
+    if (cudaGetDevice(&S->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete S;
+        return SPMV_ERR_CUDA;
+    }
+    try {
+        for (int i = 0; i < max_slots; ++i) S->workers.emplace_back(worker, S);
+    } catch (...) {
+        {
+            std::lock_guard<std::mutex> lock(S->mu);
+            S->stop = true;
+        }
+        S->cv.notify_all();
+        for (auto &t : S->workers) t.join();
+        delete S;
+        return SPMV_ERR_OOM;
+    }
+    *out = S;
+    return SPMV_OK;
 }
-spmv_status_t spmv_server_submit(spmv_server_t s, int32_t, int64_t, const int32_t *,
-                                 const int32_t *, const double *, const double *,
-                                 const cg_options_t *, uint64_t *) {
-    if (!s) return SPMV_ERR_INVALID_ARG;
-    return SPMV_ERR_UNSUPPORTED;
+
+spmv_status_t spmv_server_submit(spmv_server_t S, int32_t n, int64_t nnz, const int32_t *row_ptr,
+                                 const int32_t *col_idx, const double *values, const double *b,
+                                 const cg_options_t *opt, uint64_t *ticket) {
+    if (!S || !ticket || n < 0 || nnz < 0 || nnz > INT32_MAX || !row_ptr) return SPMV_ERR_INVALID_ARG;
+    if (n > 0 && !b) return SPMV_ERR_INVALID_ARG;
+    if (nnz > 0 && (!col_idx || !values)) return SPMV_ERR_INVALID_ARG;
+    Request *r = new (std::nothrow) Request();
+    if (!r) return SPMV_ERR_OOM;
+    try {
+        r->rp.assign(row_ptr, row_ptr + (size_t)n + 1);
+        r->ci.assign(col_idx, col_idx + nnz);
+        r->val.assign(values, values + nnz);
+        r->b.assign(b, b + n);
+    } catch (...) {
+        delete r;
+        return SPMV_ERR_OOM;
+    }
+    r->n = n;
+    r->nnz = nnz;
+    cg_default_options(&r->opt);
+    if (opt) r->opt = *opt;
+    r->est_bytes = estimate_bytes(n, nnz, r->opt.mixed != 0);
+    r->t_submit = Clock::now();
+    {
+        std::lock_guard<std::mutex> lock(S->mu);
+        if (r->est_bytes > S->budget) {
+            S->rejected += 1;
+            delete r;
+            return SPMV_ERR_BUDGET;
+        }
+        r->ticket = S->next_ticket++;
+        S->submitted += 1;
+        S->all[r->ticket] = r;
+        S->queue.push_back(r);
+        *ticket = r->ticket;
+    }
+    S->cv.notify_all();
+    return SPMV_OK;
 }
-spmv_status_t spmv_server_poll(spmv_server_t s, uint64_t, double *, cg_result_t *) {
-    if (!s) return SPMV_ERR_INVALID_ARG;
-    return SPMV_ERR_UNSUPPORTED;
+
+spmv_status_t spmv_server_poll(spmv_server_t S, uint64_t ticket, double *x_host,
+                               cg_result_t *result) {
+    if (!S) return SPMV_ERR_INVALID_ARG;
+    Request *r = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(S->mu);
+        auto it = S->all.find(ticket);
+        if (it == S->all.end()) return SPMV_ERR_INVALID_ARG;
+        if (!it->second->done) return SPMV_ERR_PENDING;
+        r = it->second;
+        S->all.erase(it);
+    }
+    if (x_host && !r->x.empty()) std::memcpy(x_host, r->x.data(), sizeof(double) * r->x.size());
+    if (result) *result = r->result;
+    const spmv_status_t s = r->status;
+    delete r;
+    return s;
 }
-spmv_status_t spmv_server_get_stats(spmv_server_t, spmv_server_stats_t *) {
-    return SPMV_ERR_UNSUPPORTED;
+
+spmv_status_t spmv_server_get_stats(spmv_server_t S, spmv_server_stats_t *st) {
+    if (!S || !st) return SPMV_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(S->mu);
+    st->submitted = S->submitted;
+    st->completed = S->completed;
+    st->rejected = S->rejected;
+    st->active_slots = S->active;
+    st->queued = (int)S->queue.size();
+    st->bytes_in_use = S->bytes_in_use;
+    st->peak_bytes = S->peak;
+    st->p50_latency_s = percentile(S->latencies, 0.50);
+    st->p99_latency_s = percentile(S->latencies, 0.99);
+    return SPMV_OK;
 }
-spmv_status_t spmv_server_destroy(spmv_server_t) { return SPMV_OK; }
+
+spmv_status_t spmv_server_destroy(spmv_server_t S) {
+    if (!S) return SPMV_OK;
+    {
+        std::lock_guard<std::mutex> lock(S->mu);
+        S->stop = true;
+    }
+    S->cv.notify_all();
+    for (auto &t : S->workers) t.join();
+    for (auto &kv : S->all) delete kv.second;
+    delete S;
+    return SPMV_OK;
+}
 
 }  // extern "C"

@@ -1,0 +1,122 @@
+"""Continuous-batching server through the C ABI: every result matches the oracle's residual
+bar, a request gives bit-identical x alone and in a mix of concurrent solves, admission never
+exceeds the memory budget, and requests that can never fit are refused."""
+import time
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2107_12371_gb300 import capi, meshgen, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    capi.load()
+    torch.cuda.init()
+
+
+def requests(sizes, seed0=0):
+    out = []
+    for i, cells in enumerate(sizes):
+        m, b = workloads.serving_request(seed0 + i, cells)
+        out.append((m, b))
+    return out
+
+
+def wait_all(srv, tickets, ms, timeout=120.0):
+    res = {}
+    t0 = time.time()
+    while len(res) < len(tickets):
+        for t, m in zip(tickets, ms):
+            if t in res:
+                continue
+            x = np.empty(m.n)
+            r = capi.spmv_server_poll(srv, t, x)
+            if r is not None:
+                res[t] = (x, r)
+        assert time.time() - t0 < timeout, "server did not finish"
+        time.sleep(0.001)
+    return [res[t] for t in tickets]
+
+
+def relres(oracle, m, x, b):
+    return np.linalg.norm(b - oracle.spmv(m.row_ptr, m.col_idx, m.values, x)) / np.linalg.norm(b)
+
+
+def test_alone_equals_in_mix(oracle):
+    reqs = requests([2e4, 8e3, 5e4, 1.2e4, 3e4, 9e3, 4e4, 2.5e4], seed0=100)
+    opts = [capi.cg_default_options(rtol=1e-8, mixed=(i % 2)) for i in range(len(reqs))]
+    # alone: one slot, one request at a time
+    alone = []
+    srv = capi.spmv_server_create(8 << 30, 1)
+    for (m, b), o in zip(reqs, opts):
+        t = capi.spmv_server_submit(srv, m.n, m.row_ptr, m.col_idx, m.values, b, o)
+        alone.append(wait_all(srv, [t], [m])[0])
+    capi.spmv_server_destroy(srv)
+    # in a mix: four slots, everything submitted at once
+    srv = capi.spmv_server_create(8 << 30, 4)
+    tickets = [capi.spmv_server_submit(srv, m.n, m.row_ptr, m.col_idx, m.values, b, o)
+               for (m, b), o in zip(reqs, opts)]
+    mixed = wait_all(srv, tickets, [m for m, _ in reqs])
+    st = capi.spmv_server_get_stats(srv)
+    capi.spmv_server_destroy(srv)
+    assert st["completed"] == len(reqs) and st["rejected"] == 0
+    assert st["p99_latency_s"] >= st["p50_latency_s"] > 0
+    for (m, b), (xa, ra), (xm, rm) in zip(reqs, alone, mixed):
+        assert ra["status"] == rm["status"] == capi.SPMV_OK
+        assert np.array_equal(xa, xm)
+        assert ra["iterations"] == rm["iterations"]
+        assert relres(oracle, m, xm, b) <= 1e-8
+
+
+def test_budget_admission_and_refusal():
+    reqs = requests([3e4, 3e4, 3e4, 3e4], seed0=7)
+    m0 = reqs[0][0]
+    # a budget that holds one of these solves but not two
+    est_one = 4 * (m0.n + 1) + 12 * m0.nnz
+    budget = 60 * m0.nnz + 120 * m0.n + (6 << 20)
+    srv = capi.spmv_server_create(budget, 4)
+    tickets = [capi.spmv_server_submit(srv, m.n, m.row_ptr, m.col_idx, m.values, b)
+               for m, b in reqs]
+    max_active = 0
+    t0 = time.time()
+    done = {}
+    while len(done) < len(tickets):
+        st = capi.spmv_server_get_stats(srv)
+        max_active = max(max_active, st["active_slots"])
+        assert st["bytes_in_use"] <= budget
+        for t, (m, b) in zip(tickets, reqs):
+            if t not in done:
+                r = capi.spmv_server_poll(srv, t, np.empty(m.n))
+                if r is not None:
+                    done[t] = r
+        assert time.time() - t0 < 120
+    st = capi.spmv_server_get_stats(srv)
+    assert st["peak_bytes"] <= budget
+    assert max_active <= 1
+    assert all(r["status"] == capi.SPMV_OK for r in done.values())
+    # a request that can never fit is refused at submit
+    big, bb = requests([2e5], seed0=3)[0]
+    with pytest.raises(capi.SpmvError) as e:
+        capi.spmv_server_submit(srv, big.n, big.row_ptr, big.col_idx, big.values, bb)
+    assert e.value.status == capi.SPMV_ERR_BUDGET
+    assert capi.spmv_server_get_stats(srv)["rejected"] == 1
+    # unknown ticket
+    assert capi.load().spmv_server_poll(srv, 10 ** 9, None, None) == capi.SPMV_ERR_INVALID_ARG
+    capi.spmv_server_destroy(srv)
+    assert est_one > 0
+
+
+def test_destroy_with_requests_in_flight():
+    reqs = requests([5e4] * 6, seed0=40)
+    srv = capi.spmv_server_create(8 << 30, 2)
+    for m, b in reqs:
+        capi.spmv_server_submit(srv, m.n, m.row_ptr, m.col_idx, m.values, b)
+    capi.spmv_server_destroy(srv)  # joins the running solves, frees the queued ones
+    torch.cuda.synchronize()
