@@ -40,6 +40,22 @@ def spmv_bytes(n, nnz, f32=False):
     return (8 * nnz + 8 * n) if f32 else (12 * nnz + 16 * n)
 
 
+def reduce_max_time(t_local, world, device=None):
+    """Slowest rank's time (replicas: every rank runs the same workload on its own GPU)."""
+    if world == 1:
+        return t_local
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([t_local], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def weak_scaling_value(nbytes_per_step, steps, world, t_max):
+    """Whole-job effective GB/s: bytes of all ranks' steps over the slowest rank's time."""
+    return world * nbytes_per_step * steps / t_max / 1e9
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -267,12 +283,8 @@ def run_gpu(args):
             stream.synchronize()
     clocks = sampler.stop()
 
-    t_dev = sum(times) / 1e3  # seconds over the K timed SpMVs
-    if world > 1:
-        tt = torch.tensor([t_dev], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_dev = float(tt.item())
-    value = world * nbytes * args.steps / t_dev / 1e9
+    t_dev = reduce_max_time(sum(times) / 1e3, world, dev)  # seconds over the K timed SpMVs
+    value = weak_scaling_value(nbytes, args.steps, world, t_dev)
     avg_launch_s = sum(times) / len(times) / 1e3
     peak, peak_src = measured_peaks()
 
@@ -385,6 +397,7 @@ def secondary(args, torch, capi, workloads, m, x, A, xi, stream, flush, dev):
                                      "unit": "GB/s", "ms": sum(t) / len(t)}
     R.close()
     out.update(cg_results(torch, capi, m, x, A, xi, dev))
+    out.update(spmm_results(args, torch, capi, workloads, flush, stream, dev))
     return out
 
 
@@ -420,6 +433,40 @@ def cg_results(torch, capi, m, b, A, bi, dev):
     if "cg_fp64_graph" in out and "cg_mixed_ir" in out:
         out["mixed_speedup_vs_fp64"] = out["cg_fp64_graph"]["seconds"] / out["cg_mixed_ir"]["seconds"]
     return out
+
+
+def spmm_results(args, torch, capi, workloads, flush, stream, dev):
+    """Multi-RHS products on the mixed hexahedron/prism/tetrahedron mesh (87^3 hexahedra,
+    about 2M cells, seed 1, RCM order), k = 8 and 32 right-hand sides, FP64 and FP32."""
+    out = {}
+    m, X = workloads.mixed(87, seed=1, k=32)
+    A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values, stream=stream,
+                    reorder=capi.SPMV_REORDER_RCM, precision=capi.SPMV_PREC_DUAL)
+    info = A.info()
+    K = max(5, min(args.steps, 30))
+    for k in (8, 32):
+        for name, dt, vb in (("f64", torch.float64, 8), ("f32", torch.float32, 4)):
+            Xd = torch.from_numpy(np.ascontiguousarray(X[:, :k])).to(dev, dt)
+            Yd = torch.empty_like(Xd)
+            t = time_kernel(torch, lambda: A.apply_multi(Xd, Yd, stream), K, flush, stream)
+            sec = sum(t) / len(t) / 1e3
+            nbytes = (vb + 4) * m.nnz + 2 * vb * m.n * k
+            flops = 2.0 * m.nnz * k
+            item = {"ms": sec * 1e3, "GBs": nbytes / sec / 1e9, "GFLOPs": flops / sec / 1e9,
+                    "algorithmic_bytes": nbytes}
+            if name == "f64":
+                item["roofline"] = {"bound": "alu", "achieved": flops / sec / 1e12, "peak": 1.25,
+                                    "unit": "TFLOP/s", "frac": flops / sec / 1e12 / 1.25,
+                                    "peak_source": "nominal GB300 FP64 rate (1.25 TFLOP/s)"}
+            else:
+                peak, _ = measured_peaks()
+                item["roofline"] = {"bound": "hbm", "achieved": nbytes / sec / 1e9, "peak": peak,
+                                    "unit": "GB/s", "frac": nbytes / sec / 1e9 / peak}
+            out["k%d_%s" % (k, name)] = item
+    A.close()
+    return {"spmm_mixed_mesh": {"n": m.n, "nnz": m.nnz, "max_row": int(np.diff(m.row_ptr).max()),
+                                "slice_height": info["slice_height"],
+                                "index_bits": info["index_bits"], **out}}
 
 
 def _make_request(args):

@@ -73,10 +73,13 @@ typedef struct {
     int autotune;        /* 1: time the candidate (S, block, variant) on this matrix and keep the fastest */
     int peripheral;      /* 1: George-Liu pseudo-peripheral start node for (R)CM             */
     int window_words;    /* SELL_WINDOW capacity in x entries per CTA (0 = largest that fits) */
+    int index_bits;      /* 0 = 16 when every slice spans < 65,535 columns, else 32;
+                          * 32 = always int32 columns; 16 = 16-bit where possible.  16-bit
+                          * columns are offsets from the slice's col_start (Sec. 5.1). */
 } spmv_options_t;
 
 /* Fills *opt with the defaults (S = 64, block = 256, AUTO variant, no reordering, FP64,
- * no autotuning, peripheral start on).  Returns SPMV_ERR_INVALID_ARG if opt is NULL. */
+ * no autotuning, peripheral start on, automatic column index width).  Returns SPMV_ERR_INVALID_ARG if opt is NULL. */
 spmv_status_t spmv_default_options(spmv_options_t *opt);
 
 /* Human-readable name of a status code (static string, never NULL). */
@@ -116,6 +119,7 @@ typedef struct {
     int32_t max_slice_span;  /* max over slices of col_end - col_start            */
     int32_t window_words;    /* shared-memory window capacity (SELL_WINDOW), else 0 */
     size_t device_bytes;     /* device memory owned by the handle                 */
+    int32_t index_bits;      /* 32 or 16 (column indices streamed by the kernels) */
 } spmv_info_t;
 spmv_status_t spmv_get_info(spmv_matrix_t A, spmv_info_t *info);
 

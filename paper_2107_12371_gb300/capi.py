@@ -36,7 +36,8 @@ class spmv_options_t(ctypes.Structure):
     _fields_ = [("slice_height", ctypes.c_int), ("block", ctypes.c_int),
                 ("variant", ctypes.c_int), ("reorder", ctypes.c_int),
                 ("precision", ctypes.c_int), ("autotune", ctypes.c_int),
-                ("peripheral", ctypes.c_int), ("window_words", ctypes.c_int)]
+                ("peripheral", ctypes.c_int), ("window_words", ctypes.c_int),
+                ("index_bits", ctypes.c_int)]
 
 
 class spmv_info_t(ctypes.Structure):
@@ -46,7 +47,7 @@ class spmv_info_t(ctypes.Structure):
                 ("reorder", ctypes.c_int32), ("n_slices", ctypes.c_int32),
                 ("sell_entries", ctypes.c_int64), ("bandwidth", ctypes.c_int32),
                 ("max_slice_span", ctypes.c_int32), ("window_words", ctypes.c_int32),
-                ("device_bytes", ctypes.c_size_t)]
+                ("device_bytes", ctypes.c_size_t), ("index_bits", ctypes.c_int32)]
 
 
 class cg_options_t(ctypes.Structure):

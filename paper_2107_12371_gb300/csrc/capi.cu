@@ -50,6 +50,7 @@ static spmv_status_t normalize_options(const spmv_options_t *in, spmv_options_t 
     if (o->reorder < SPMV_REORDER_NONE || o->reorder > SPMV_REORDER_CM) return SPMV_ERR_INVALID_ARG;
     if (o->precision < SPMV_PREC_FP64 || o->precision > SPMV_PREC_DUAL) return SPMV_ERR_INVALID_ARG;
     if (o->window_words < 0) return SPMV_ERR_INVALID_ARG;
+    if (o->index_bits != 0 && o->index_bits != 16 && o->index_bits != 32) return SPMV_ERR_INVALID_ARG;
     return SPMV_OK;
 }
 
@@ -73,6 +74,7 @@ spmv_status_t spmv_default_options(spmv_options_t *opt) {
     opt->autotune = 0;
     opt->peripheral = 1;
     opt->window_words = 0;
+    opt->index_bits = 0;
     return SPMV_OK;
 }
 
@@ -183,6 +185,7 @@ spmv_status_t spmv_get_info(spmv_matrix_t A, spmv_info_t *info) {
     info->max_slice_span = A->max_span;
     info->window_words = A->window_words;
     info->device_bytes = A->bytes;
+    info->index_bits = A->index_bits;
     return SPMV_OK;
 }
 
@@ -297,6 +300,7 @@ void release_matrix(spmv_matrix_t A) {
     A->val32.release(t);
     A->slice_ptr.release(t);
     A->sell_col.release(t);
+    A->sell_col16.release(t);
     A->sell_val.release(t);
     A->sell_val32.release(t);
     A->col_start.release(t);

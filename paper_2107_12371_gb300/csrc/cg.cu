@@ -45,9 +45,9 @@ __global__ void cg_dinv(int32_t n, const int32_t *rp, const int32_t *ci, const d
 // r = b - A x (x_zero: r = b), p = D^-1 r (if p), partials r.(D^-1 r), r.r, b.b.
 // Last CTA: rho, rr, bb, s = ||r||, done = rr <= tol2 bb.  Used to start and to restart CG,
 // and for the FP64 residual of iterative refinement (p == nullptr).
-template <typename T, int R, int L>
+template <typename T, int R, int L, typename ColT>
 __global__ void __launch_bounds__(kCgBlock)
-cg_residual(int32_t n, int32_t n_slices, const int64_t *sp, const int32_t *col, const T *val,
+cg_residual(int32_t n, int32_t n_slices, const int64_t *sp, ColT col, const T *val,
             const T *x, int x_zero, const T *b, T *r, T *p, const T *dinv, double *part,
             CgScalars *sc) {
     constexpr int S = L * R;
@@ -93,9 +93,9 @@ cg_residual(int32_t n, int32_t n_slices, const int64_t *sp, const int32_t *col, 
 }
 
 // q = A p; partial p.q; last CTA: alpha = rho / (p.q)
-template <typename T, int R, int L>
+template <typename T, int R, int L, typename ColT>
 __global__ void __launch_bounds__(kCgBlock)
-cg_spmv_pq(int32_t n, int32_t n_slices, const int64_t *sp, const int32_t *col, const T *val,
+cg_spmv_pq(int32_t n, int32_t n_slices, const int64_t *sp, ColT col, const T *val,
            const T *p, T *q, double *part, CgScalars *sc) {
     if (sc->done) return;
     constexpr int S = L * R;
@@ -253,23 +253,33 @@ spmv_status_t ensure_cg_work(spmv_matrix_t A, bool mixed, cudaStream_t st) {
 static CgScalars *outer_scalars(spmv_matrix_t A) { return (CgScalars *)A->cg.scal.p; }
 static CgScalars *inner_scalars(spmv_matrix_t A) { return (CgScalars *)A->cg.scal.p + 1; }
 
+// column-index format of the handle's sliced ELLPACK (see spmv.cu)
+template <typename F>
+static spmv_status_t with_cols(spmv_matrix_t A, F &&f) {
+    if (A->index_bits == 16) return f(Cols16{A->sell_col16.p, A->col_start.p});
+    return f(Cols32{A->sell_col.p});
+}
+
 // enqueue `iters` FP64 iterations (3 kernels each)
 static spmv_status_t enqueue_cg64(spmv_matrix_t A, int iters, cudaStream_t st) {
     CgWork &w = A->cg;
     const int G = cg_grid();
     CgScalars *sc = outer_scalars(A);
-    return with_shape(A->S, false, [&](auto rt, auto lt) -> spmv_status_t {
-        constexpr int R = decltype(rt)::value, L = decltype(lt)::value;
-        for (int it = 0; it < iters; ++it) {
-            cg_spmv_pq<double, R, L><<<G, kCgBlock, 0, st>>>(A->n, A->n_slices, A->slice_ptr.p,
-                                                             A->sell_col.p, A->sell_val.p, w.p.p,
-                                                             w.q.p, w.part.p, sc);
-            cg_update_xr<double><<<G, kCgBlock, 0, st>>>(A->n, w.x.p, w.r.p, w.p.p, w.q.p,
-                                                         w.dinv.p, w.part.p + G, sc);
-            cg_update_p<double><<<G, kCgBlock, 0, st>>>(A->n, w.r.p, w.dinv.p, w.p.p, sc);
-        }
-        GB_LAUNCHED();
-        return SPMV_OK;
+    return with_cols(A, [&](auto cols) -> spmv_status_t {
+        using ColT = decltype(cols);
+        return with_shape(A->S, false, [&](auto rt, auto lt) -> spmv_status_t {
+            constexpr int R = decltype(rt)::value, L = decltype(lt)::value;
+            for (int it = 0; it < iters; ++it) {
+                cg_spmv_pq<double, R, L, ColT><<<G, kCgBlock, 0, st>>>(
+                    A->n, A->n_slices, A->slice_ptr.p, cols, A->sell_val.p, w.p.p, w.q.p, w.part.p,
+                    sc);
+                cg_update_xr<double><<<G, kCgBlock, 0, st>>>(A->n, w.x.p, w.r.p, w.p.p, w.q.p,
+                                                             w.dinv.p, w.part.p + G, sc);
+                cg_update_p<double><<<G, kCgBlock, 0, st>>>(A->n, w.r.p, w.dinv.p, w.p.p, sc);
+            }
+            GB_LAUNCHED();
+            return SPMV_OK;
+        });
     });
 }
 
@@ -277,18 +287,21 @@ static spmv_status_t enqueue_cg32(spmv_matrix_t A, int iters, cudaStream_t st) {
     CgWork &w = A->cg;
     const int G = cg_grid();
     CgScalars *sc = inner_scalars(A);
-    return with_shape(A->S, true, [&](auto rt, auto lt) -> spmv_status_t {
-        constexpr int R = decltype(rt)::value, L = decltype(lt)::value;
-        for (int it = 0; it < iters; ++it) {
-            cg_spmv_pq<float, R, L><<<G, kCgBlock, 0, st>>>(A->n, A->n_slices, A->slice_ptr.p,
-                                                            A->sell_col.p, A->sell_val32.p,
-                                                            w.p32.p, w.q32.p, w.part.p, sc);
-            cg_update_xr<float><<<G, kCgBlock, 0, st>>>(A->n, w.d32.p, w.r32.p, w.p32.p, w.q32.p,
-                                                        w.dinv32.p, w.part.p + G, sc);
-            cg_update_p<float><<<G, kCgBlock, 0, st>>>(A->n, w.r32.p, w.dinv32.p, w.p32.p, sc);
-        }
-        GB_LAUNCHED();
-        return SPMV_OK;
+    return with_cols(A, [&](auto cols) -> spmv_status_t {
+        using ColT = decltype(cols);
+        return with_shape(A->S, true, [&](auto rt, auto lt) -> spmv_status_t {
+            constexpr int R = decltype(rt)::value, L = decltype(lt)::value;
+            for (int it = 0; it < iters; ++it) {
+                cg_spmv_pq<float, R, L, ColT><<<G, kCgBlock, 0, st>>>(
+                    A->n, A->n_slices, A->slice_ptr.p, cols, A->sell_val32.p, w.p32.p, w.q32.p,
+                    w.part.p, sc);
+                cg_update_xr<float><<<G, kCgBlock, 0, st>>>(A->n, w.d32.p, w.r32.p, w.p32.p,
+                                                            w.q32.p, w.dinv32.p, w.part.p + G, sc);
+                cg_update_p<float><<<G, kCgBlock, 0, st>>>(A->n, w.r32.p, w.dinv32.p, w.p32.p, sc);
+            }
+            GB_LAUNCHED();
+            return SPMV_OK;
+        });
     });
 }
 
@@ -297,13 +310,16 @@ static spmv_status_t enqueue_residual64(spmv_matrix_t A, const double *b, bool x
                                         bool want_p, cudaStream_t st) {
     CgWork &w = A->cg;
     const int G = cg_grid();
-    return with_shape(A->S, false, [&](auto rt, auto lt) -> spmv_status_t {
-        constexpr int R = decltype(rt)::value, L = decltype(lt)::value;
-        cg_residual<double, R, L><<<G, kCgBlock, 0, st>>>(
-            A->n, A->n_slices, A->slice_ptr.p, A->sell_col.p, A->sell_val.p, w.x.p,
-            x_zero ? 1 : 0, b, w.r.p, want_p ? w.p.p : nullptr, w.dinv.p, w.part.p, outer_scalars(A));
-        GB_LAUNCHED();
-        return SPMV_OK;
+    return with_cols(A, [&](auto cols) -> spmv_status_t {
+        using ColT = decltype(cols);
+        return with_shape(A->S, false, [&](auto rt, auto lt) -> spmv_status_t {
+            constexpr int R = decltype(rt)::value, L = decltype(lt)::value;
+            cg_residual<double, R, L, ColT><<<G, kCgBlock, 0, st>>>(
+                A->n, A->n_slices, A->slice_ptr.p, cols, A->sell_val.p, w.x.p, x_zero ? 1 : 0, b,
+                w.r.p, want_p ? w.p.p : nullptr, w.dinv.p, w.part.p, outer_scalars(A));
+            GB_LAUNCHED();
+            return SPMV_OK;
+        });
     });
 }
 

@@ -91,15 +91,16 @@ __device__ bool grid_sum_last(double (&v)[NV], double *part, unsigned *ticket, d
 // y-rows (R of them) of lane `lane` in slice `slice`: sum over the slice's columns in order,
 // fused multiply-add from +0.0, padding skipped (the same order as spmv_sell).  COHERENT
 // selects coherent gathers of x, for kernels in which other CTAs rewrite x between barriers.
-template <typename T, int R, int L, bool COHERENT = false>
+template <typename T, int R, int L, bool COHERENT = false, typename ColT>
 __device__ __forceinline__ void slice_rows(int64_t slice, int lane, const int64_t *sp,
-                                           const int32_t *col, const T *val, const T *x,
+                                           const ColT &cols, const T *val, const T *x,
                                            uint64_t pol, T (&acc)[R]) {
     constexpr int S = L * R;
     const int64_t base = sp[slice];
     const int w = (int)((sp[slice + 1] - base) / S);
+    const int32_t cbase = cols.base(slice);
     const T *vp = val + base + lane * R;
-    const int32_t *cp = col + base + lane * R;
+    const int64_t cat = base + lane * R;
 #pragma unroll
     for (int i = 0; i < R; ++i) acc[i] = T(0);
     int t = 0;
@@ -107,9 +108,9 @@ __device__ __forceinline__ void slice_rows(int64_t slice, int lane, const int64_
         T v[2][R];
         int32_t c[2][R];
         ld_stream(vp + (int64_t)t * S, pol, v[0]);
-        ld_stream(cp + (int64_t)t * S, pol, c[0]);
+        cols.template load<R>(cat + (int64_t)t * S, slice, pol, cbase, c[0]);
         ld_stream(vp + (int64_t)(t + 1) * S, pol, v[1]);
-        ld_stream(cp + (int64_t)(t + 1) * S, pol, c[1]);
+        cols.template load<R>(cat + (int64_t)(t + 1) * S, slice, pol, cbase, c[1]);
         T xv[2][R];
 #pragma unroll
         for (int u = 0; u < 2; ++u)
@@ -127,7 +128,7 @@ __device__ __forceinline__ void slice_rows(int64_t slice, int lane, const int64_
         T v[R];
         int32_t c[R];
         ld_stream(vp + (int64_t)t * S, pol, v);
-        ld_stream(cp + (int64_t)t * S, pol, c);
+        cols.template load<R>(cat + (int64_t)t * S, slice, pol, cbase, c);
 #pragma unroll
         for (int i = 0; i < R; ++i)
             if (c[i] >= 0)

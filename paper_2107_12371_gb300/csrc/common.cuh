@@ -119,6 +119,7 @@ struct spmv_matrix_s {
     int block = 256;   // threads per CTA
     int variant = SPMV_VARIANT_SELL;
     int window_words = 0;
+    int index_bits = 32;  // 16: sell_col16 holds offsets from the slice's col_start
     int32_t bandwidth = 0;
     int32_t max_span = 0;
     int32_t n_slices = 0;
@@ -132,6 +133,7 @@ struct spmv_matrix_s {
     gb::DevBuf<float> val32;
     gb::DevBuf<int64_t> slice_ptr;  // sliced ELLPACK
     gb::DevBuf<int32_t> sell_col;
+    gb::DevBuf<uint16_t> sell_col16;  // 16-bit relative columns (Sec. 5.1), 0xFFFF = padding
     gb::DevBuf<double> sell_val;
     gb::DevBuf<float> sell_val32;
     gb::DevBuf<int32_t> col_start;  // per-slice x range (Sec. 5.1)

@@ -469,6 +469,19 @@ __global__ void window_meta(int32_t n_slices, int32_t S, const int64_t *sp, cons
     (void)S;
 }
 
+// 16-bit columns relative to the slice's first column (Sec. 5.1); padding -> 0xFFFF
+__global__ void relative_cols16(int32_t n_slices, const int64_t *sp, const int32_t *scol,
+                                const int32_t *cs, uint16_t *out) {
+    const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (s >= n_slices) return;
+    const int32_t base = cs[s];
+    for (int64_t at = sp[s] + lane; at < sp[s + 1]; at += 32) {
+        const int32_t c = scol[at];
+        out[at] = c < 0 ? (uint16_t)0xFFFFu : (uint16_t)(c - base);
+    }
+}
+
 }  // namespace
 
 spmv_status_t build_sell(spmv_matrix_t A, int S, cudaStream_t st) {
@@ -519,8 +532,20 @@ spmv_status_t build_sell(spmv_matrix_t A, int S, cudaStream_t st) {
         s = cuda_status(cudaMemcpyAsync(&span, d_span, sizeof(int), cudaMemcpyDeviceToHost, st));
     cudaFreeAsync(d_span, st);
     if (s == SPMV_OK) s = cuda_status(cudaStreamSynchronize(st));
+    if (s != SPMV_OK) return s;
     A->max_span = span;
-    return s;
+    // 16-bit relative columns when every slice spans fewer than 65,535 columns
+    const int want = A->opt.index_bits;
+    A->sell_col16.release(tally);
+    A->index_bits = 32;
+    if (want != 32 && span < 65535 && total > 0) {
+        GB_TRY(A->sell_col16.alloc((size_t)total, tally));
+        relative_cols16<<<blocks_for((int64_t)n_slices * 32), kT, 0, st>>>(
+            n_slices, A->slice_ptr.p, A->sell_col.p, A->col_start.p, A->sell_col16.p);
+        GB_LAUNCHED();
+        A->index_bits = 16;
+    }
+    return SPMV_OK;
 }
 
 spmv_status_t build_matrix(spmv_matrix_t A, const int32_t *d_rp, const int32_t *d_ci,

@@ -74,9 +74,9 @@ __device__ void store_parts(double (&v)[NV], double *part) {
     }
 }
 
-template <int R, int L>
+template <int R, int L, typename ColT>
 __global__ void __launch_bounds__(kCgBlock, kCgCtasPerSm)
-cg_persistent(int32_t n, int32_t n_slices, const int64_t *sp, const int32_t *col,
+cg_persistent(int32_t n, int32_t n_slices, const int64_t *sp, ColT col,
               const double *val, double *x, double *r, double *p, double *q, const double *dinv,
               double *part, CgScalars *sc) {
     constexpr int S = L * R;
@@ -170,32 +170,36 @@ spmv_status_t cg_persistent64(spmv_matrix_t A, const cg_options_t &o, CgScalars 
                               cudaStream_t st) {
     CgWork &w = A->cg;
     CgScalars *sc = (CgScalars *)w.scal.p;
-    return with_shape(A->S, false, [&](auto rt, auto lt) -> spmv_status_t {
-        constexpr int R = decltype(rt)::value, L = decltype(lt)::value;
-        auto kern = cg_persistent<R, L>;
-        if (w.pers_grid == 0) {
+    auto launch = [&](auto cols) -> spmv_status_t {
+        using ColT = decltype(cols);
+        return with_shape(A->S, false, [&](auto rt, auto lt) -> spmv_status_t {
+            constexpr int R = decltype(rt)::value, L = decltype(lt)::value;
+            auto kern = cg_persistent<R, L, ColT>;
             int per_sm = 0;
             GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCgBlock, 0));
             // the grid must be co-resident and equal to the graph path's grid
             if (per_sm < kCgCtasPerSm) return SPMV_ERR_UNSUPPORTED;
             w.pers_grid = cg_grid();
-        }
-        const long long budget = o.timeout_s > 0 ? (long long)(o.timeout_s * 1e9) : 0;
-        GB_CUDA(cudaMemcpyAsync(&sc->budget_ns, &budget, sizeof(budget), cudaMemcpyHostToDevice, st));
-        int32_t n = A->n, ns = A->n_slices;
-        const int64_t *sp = A->slice_ptr.p;
-        const int32_t *col = A->sell_col.p;
-        const double *val = A->sell_val.p;
-        double *x = w.x.p, *r = w.r.p, *p = w.p.p, *q = w.q.p, *part = w.part.p;
-        const double *dinv = w.dinv.p;
-        void *args[] = {&n, &ns, &sp, &col, &val, &x, &r, &p, &q, &dinv, &part, &sc};
-        GB_CUDA(cudaLaunchCooperativeKernel((const void *)kern, dim3(w.pers_grid), dim3(kCgBlock),
-                                            args, 0, st));
-        GB_CUDA(cudaMemcpyAsync(w.h_scal, w.scal.p, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
-        GB_CUDA(cudaStreamSynchronize(st));
-        *out = w.h_scal[0];
-        return SPMV_OK;
-    });
+            const long long budget = o.timeout_s > 0 ? (long long)(o.timeout_s * 1e9) : 0;
+            GB_CUDA(cudaMemcpyAsync(&sc->budget_ns, &budget, sizeof(budget),
+                                    cudaMemcpyHostToDevice, st));
+            int32_t n = A->n, ns = A->n_slices;
+            const int64_t *sp = A->slice_ptr.p;
+            const double *val = A->sell_val.p;
+            double *x = w.x.p, *r = w.r.p, *p = w.p.p, *q = w.q.p, *part = w.part.p;
+            const double *dinv = w.dinv.p;
+            void *args[] = {&n, &ns, &sp, &cols, &val, &x, &r, &p, &q, &dinv, &part, &sc};
+            GB_CUDA(cudaLaunchCooperativeKernel((const void *)kern, dim3(w.pers_grid),
+                                                dim3(kCgBlock), args, 0, st));
+            GB_CUDA(cudaMemcpyAsync(w.h_scal, w.scal.p, sizeof(CgScalars), cudaMemcpyDeviceToHost,
+                                    st));
+            GB_CUDA(cudaStreamSynchronize(st));
+            *out = w.h_scal[0];
+            return SPMV_OK;
+        });
+    };
+    if (A->index_bits == 16) return launch(Cols16{A->sell_col16.p, A->col_start.p});
+    return launch(Cols32{A->sell_col.p});
 }
 
 }  // namespace gb

@@ -93,6 +93,71 @@ __device__ __forceinline__ void ld_stream(const int32_t *p, uint64_t, int32_t (&
         : "l"(p));
 }
 
+// ---- streamed 16-bit relative column indices (Sec. 5.1: columns rewritten relative to the
+// slice's first column, 2 bytes instead of 4).  0xFFFF marks padding (-1 after decoding).
+__device__ __forceinline__ int32_t decode_rel16(uint32_t rel, int32_t base) {
+    return rel == 0xFFFFu ? -1 : base + (int32_t)rel;
+}
+__device__ __forceinline__ void ld_stream_rel16(const uint16_t *p, uint64_t pol, int32_t base,
+                                                int32_t (&c)[1]) {
+    uint16_t v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.b16 %0, [%1], %2;"
+        : "=h"(v) : "l"(p), "l"(pol));
+    c[0] = decode_rel16(v, base);
+}
+__device__ __forceinline__ void ld_stream_rel16(const uint16_t *p, uint64_t pol, int32_t base,
+                                                int32_t (&c)[2]) {
+    uint32_t v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.b32 %0, [%1], %2;"
+        : "=r"(v) : "l"(p), "l"(pol));
+    c[0] = decode_rel16(v & 0xFFFFu, base);
+    c[1] = decode_rel16(v >> 16, base);
+}
+__device__ __forceinline__ void ld_stream_rel16(const uint16_t *p, uint64_t pol, int32_t base,
+                                                int32_t (&c)[4]) {
+    uint32_t a, b;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.b32 {%0,%1}, [%2], %3;"
+        : "=r"(a), "=r"(b) : "l"(p), "l"(pol));
+    c[0] = decode_rel16(a & 0xFFFFu, base);
+    c[1] = decode_rel16(a >> 16, base);
+    c[2] = decode_rel16(b & 0xFFFFu, base);
+    c[3] = decode_rel16(b >> 16, base);
+}
+__device__ __forceinline__ void ld_stream_rel16(const uint16_t *p, uint64_t pol, int32_t base,
+                                                int32_t (&c)[8]) {
+    uint32_t a, b, d, e;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.b32 {%0,%1,%2,%3}, [%4], %5;"
+        : "=r"(a), "=r"(b), "=r"(d), "=r"(e) : "l"(p), "l"(pol));
+    const uint32_t w[4] = {a, b, d, e};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        c[2 * k] = decode_rel16(w[k] & 0xFFFFu, base);
+        c[2 * k + 1] = decode_rel16(w[k] >> 16, base);
+    }
+}
+
+// Column indices of a slice: 32-bit absolute, or 16-bit relative to the slice's col_start.
+struct Cols32 {
+    const int32_t *col;
+    template <int R>
+    __device__ __forceinline__ void load(int64_t at, int64_t, uint64_t pol, int32_t base,
+                                         int32_t (&c)[R]) const {
+        (void)base;
+        ld_stream(col + at, pol, c);
+    }
+    __device__ __forceinline__ int32_t base(int64_t) const { return 0; }
+};
+struct Cols16 {
+    const uint16_t *col;
+    const int32_t *col_start;
+    template <int R>
+    __device__ __forceinline__ void load(int64_t at, int64_t, uint64_t pol, int32_t base,
+                                         int32_t (&c)[R]) const {
+        ld_stream_rel16(col + at, pol, base, c);
+    }
+    __device__ __forceinline__ int32_t base(int64_t slice) const { return col_start[slice]; }
+};
+
 // ---- gathers of the multiplying vector (read-only path, L1 allocating) ----------------
 // Only for vectors that no thread writes while the kernel runs.
 __device__ __forceinline__ double ld_x(const double *p) { return __ldg(p); }

@@ -7,7 +7,9 @@
 //   through the read-only L1 path; with a banded (Cuthill-McKee) order the gathers of
 //   neighbouring rows hit the same lines (Sec. 4.3, 5.1).  Each row accumulates its entries
 //   in ascending column order with fused multiply-add from +0.0; padding entries (column -1)
-//   are skipped.
+//   are skipped.  Column indices come as int32 or (when every slice spans fewer than 65,535
+//   columns) as 16-bit offsets from the slice's col_start (Sec. 5.1), 10 instead of 12 bytes
+//   per FP64 non-zero.
 // spmv_csr: the naive baseline of Sec. 4.3, thread per CSR row.
 // spmm_sell<T, G, C>: Y = A X for row-major X, G lanes per row, each lane C columns; every
 //   gathered row of X (k contiguous values) is read once per matrix entry and used for all k
@@ -18,11 +20,10 @@
 namespace gb {
 namespace {
 
-template <typename T, int R, int L, int U>
+template <typename T, int R, int L, int U, typename ColT>
 __global__ void __launch_bounds__(1024)
-spmv_sell(int32_t n, int32_t n_slices, const int64_t *__restrict__ sp,
-          const int32_t *__restrict__ col, const T *__restrict__ val, const T *__restrict__ x,
-          T *__restrict__ y) {
+spmv_sell(int32_t n, int32_t n_slices, const int64_t *__restrict__ sp, ColT cols,
+          const T *__restrict__ val, const T *__restrict__ x, T *__restrict__ y) {
     // L lanes per slice, R rows per lane: S = L R rows per slice
     constexpr int S = L * R;
     const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -31,8 +32,9 @@ spmv_sell(int32_t n, int32_t n_slices, const int64_t *__restrict__ sp,
     if (slice >= n_slices) return;
     const int64_t base = sp[slice];
     const int w = (int)((sp[slice + 1] - base) / S);
+    const int32_t cbase = cols.base(slice);
     const T *vp = val + base + lane * R;
-    const int32_t *cp = col + base + lane * R;
+    const int64_t cat = base + lane * R;
     const uint64_t pol = policy_evict_first();
     T acc[R];
 #pragma unroll
@@ -44,7 +46,7 @@ spmv_sell(int32_t n, int32_t n_slices, const int64_t *__restrict__ sp,
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             ld_stream(vp + (int64_t)(t + u) * S, pol, v[u]);
-            ld_stream(cp + (int64_t)(t + u) * S, pol, c[u]);
+            cols.template load<R>(cat + (int64_t)(t + u) * S, slice, pol, cbase, c[u]);
         }
         T xv[U][R];
 #pragma unroll
@@ -61,7 +63,7 @@ spmv_sell(int32_t n, int32_t n_slices, const int64_t *__restrict__ sp,
         T v[R];
         int32_t c[R];
         ld_stream(vp + (int64_t)t * S, pol, v);
-        ld_stream(cp + (int64_t)t * S, pol, c);
+        cols.template load<R>(cat + (int64_t)t * S, slice, pol, cbase, c);
 #pragma unroll
         for (int i = 0; i < R; ++i)
             if (c[i] >= 0) acc[i] = fma_t(v[i], ld_x(x + c[i]), acc[i]);
@@ -83,11 +85,10 @@ spmv_csr(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ 
 }
 
 // SpMM: G lanes per row (G divides 32), lane owns columns g, g + G, ... (C of them)
-template <typename T, int G, int C>
+template <typename T, int G, int C, typename ColT>
 __global__ void __launch_bounds__(256)
 spmm_sell(int32_t n, int32_t S, int32_t n_slices, int k, const int64_t *__restrict__ sp,
-          const int32_t *__restrict__ col, const T *__restrict__ val, const T *__restrict__ X,
-          T *__restrict__ Y) {
+          ColT cols, const T *__restrict__ val, const T *__restrict__ X, T *__restrict__ Y) {
     constexpr int RPW = 32 / G;  // rows per warp step
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -99,6 +100,7 @@ spmm_sell(int32_t n, int32_t S, int32_t n_slices, int k, const int64_t *__restri
     const int64_t r = row - slice * S;
     const int64_t base = sp[slice];
     const int w = (int)((sp[slice + 1] - base) / S);
+    const int32_t cbase = cols.base(slice);
     const uint64_t pol = policy_evict_first();
     T acc[C];
 #pragma unroll
@@ -107,7 +109,7 @@ spmm_sell(int32_t n, int32_t S, int32_t n_slices, int k, const int64_t *__restri
         T a[1];
         int32_t c[1];
         ld_stream(val + base + (int64_t)t * S + r, pol, a);
-        ld_stream(col + base + (int64_t)t * S + r, pol, c);
+        cols.template load<1>(base + (int64_t)t * S + r, slice, pol, cbase, c);
         if (c[0] < 0) continue;
         const T *xr = X + (int64_t)c[0] * k;
 #pragma unroll
@@ -145,8 +147,12 @@ template <typename T, int R, int L, int U>
 spmv_status_t go_sell(spmv_matrix_t A, const T *val, const T *x, T *y, cudaStream_t st) {
     const int block = A->block;
     const unsigned grid = grid_for((int64_t)A->n_slices * L, block);
-    spmv_sell<T, R, L, U><<<grid, block, 0, st>>>(A->n, A->n_slices, A->slice_ptr.p,
-                                                  A->sell_col.p, val, x, y);
+    if (A->index_bits == 16)
+        spmv_sell<T, R, L, U, Cols16><<<grid, block, 0, st>>>(
+            A->n, A->n_slices, A->slice_ptr.p, Cols16{A->sell_col16.p, A->col_start.p}, val, x, y);
+    else
+        spmv_sell<T, R, L, U, Cols32><<<grid, block, 0, st>>>(
+            A->n, A->n_slices, A->slice_ptr.p, Cols32{A->sell_col.p}, val, x, y);
     GB_LAUNCHED();
     return SPMV_OK;
 }
@@ -182,8 +188,14 @@ spmv_status_t launch_spmm(spmv_matrix_t A, int k, const T *val, const T *X, T *Y
         constexpr int G = decltype(gtag)::value;
         constexpr int C = decltype(ctag)::value;
         const int64_t warps = (rows_total + (32 / G) - 1) / (32 / G);
-        spmm_sell<T, G, C><<<grid_for(warps * 32, block), block, 0, st>>>(
-            A->n, A->S, A->n_slices, k, A->slice_ptr.p, A->sell_col.p, val, X, Y);
+        const unsigned grid = grid_for(warps * 32, block);
+        if (A->index_bits == 16)
+            spmm_sell<T, G, C, Cols16><<<grid, block, 0, st>>>(
+                A->n, A->S, A->n_slices, k, A->slice_ptr.p, Cols16{A->sell_col16.p, A->col_start.p},
+                val, X, Y);
+        else
+            spmm_sell<T, G, C, Cols32><<<grid, block, 0, st>>>(
+                A->n, A->S, A->n_slices, k, A->slice_ptr.p, Cols32{A->sell_col.p}, val, X, Y);
         GB_LAUNCHED();
         return SPMV_OK;
     };

@@ -53,9 +53,10 @@ def test_fp64_pcg_matches_oracle(oracle, n):
     assert np.linalg.norm(x - xo) <= 1e-7 * np.linalg.norm(xo)
 
 
-def test_persistent_equals_graph_path(oracle):
+@pytest.mark.parametrize("bits", [16, 32])
+def test_persistent_equals_graph_path(oracle, bits):
     m, b = workloads.kuhn(12, seed=4, dirichlet=True)
-    A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values)
+    A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values, index_bits=bits)
     x1, r1 = solve(A, b, rtol=1e-10)
     x2, r2 = solve(A, b, rtol=1e-10, persistent=1)
     assert r1["status"] == r2["status"] == capi.SPMV_OK

@@ -68,12 +68,53 @@ def ragged_matrix(n, seed, max_len=40, empty_frac=0.1):
     return meshgen.CsrMatrix(n, rp.astype(np.int32), cols.astype(np.int32), vals)
 
 
+@pytest.mark.parametrize("bits", [16, 32])
 @pytest.mark.parametrize("S", [32, 64, 128, 256])
-def test_c1_fp64_parity(oracle, S):
+def test_c1_fp64_parity(oracle, S, bits):
     m, x = workloads.c1()
     A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values, slice_height=S,
-                    variant=capi.SPMV_VARIANT_SELL)
+                    variant=capi.SPMV_VARIANT_SELL, index_bits=bits)
+    assert A.info()["index_bits"] == bits
     check_fp64(m, x, gpu_spmv(A, x), oracle)
+
+
+def test_wide_slices_fall_back_to_32bit_columns(oracle):
+    """16-bit relative columns (Sec. 5.1) only hold slices spanning < 65,535 columns."""
+    n = 70000
+    rng = np.random.default_rng(9)
+    rows = [np.array([0, n - 1])] + [np.sort(rng.choice(n, 3, replace=False)) for _ in range(n - 1)]
+    rp = np.zeros(n + 1, np.int32)
+    rp[1:] = np.cumsum([r.size for r in rows])
+    ci = np.concatenate(rows).astype(np.int32)
+    m = meshgen.CsrMatrix(n, rp, ci, rng.uniform(-1, 1, ci.size))
+    x = rng.uniform(-1, 1, n)
+    A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values)
+    assert A.info()["index_bits"] == 32
+    check_fp64(m, x, gpu_spmv(A, x), oracle)
+
+
+@pytest.mark.parametrize("precision", [capi.SPMV_PREC_FP64, capi.SPMV_PREC_FP32])
+def test_autotuned_handle_parity(oracle, precision):
+    """The autotuner times every (S, CTA size, variant) candidate on the matrix and rebuilds
+    the format for the winner; the product is unchanged bit for bit."""
+    m, x = workloads.kuhn(24, seed=5, dirichlet=True)
+    A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values, autotune=1, precision=precision,
+                    reorder=capi.SPMV_REORDER_RCM)
+    info = A.info()
+    assert info["slice_height"] in (32, 64, 128, 256) and info["block"] in (128, 256, 512)
+    assert info["variant"] in (capi.SPMV_VARIANT_SELL, capi.SPMV_VARIANT_CSR)
+    rp, ci, v = capi.spmv_export_csr(A.handle, m.n, m.nnz)
+    mi = meshgen.CsrMatrix(m.n, rp, ci, v)
+    xi = x[A.permutation()]
+    if precision == capi.SPMV_PREC_FP64:
+        check_fp64(mi, xi, gpu_spmv(A, xi), oracle)
+    else:
+        x32 = xi.astype(np.float32)
+        ref = oracle.spmv_f32(rp, ci, v.astype(np.float32), x32, use_fma=True)
+        assert np.array_equal(gpu_spmv(A, x32, f32=True), ref)
+    sp, col, _, cs, ce = capi.spmv_export_sell(A.handle, with_values=False)
+    osp, ocol, _ = oracle.sell(rp, ci, v, info["slice_height"])
+    assert np.array_equal(sp, osp) and np.array_equal(col, ocol)
 
 
 def test_c1_naive_csr_parity(oracle):
@@ -82,11 +123,12 @@ def test_c1_naive_csr_parity(oracle):
     check_fp64(m, x, gpu_spmv(A, x, csr=True), oracle)
 
 
-@pytest.mark.parametrize("S", [32, 128])
-def test_c1_fp32_parity(oracle, S):
+@pytest.mark.parametrize("bits", [16, 32])
+@pytest.mark.parametrize("S", [32, 64, 128, 256])
+def test_c1_fp32_parity(oracle, S, bits):
     m, x = workloads.c1()
     A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values, slice_height=S,
-                    precision=capi.SPMV_PREC_DUAL)
+                    precision=capi.SPMV_PREC_DUAL, index_bits=bits)
     x32 = x.astype(np.float32)
     y = gpu_spmv(A, x32, f32=True)
     ref = oracle.spmv_f32(m.row_ptr, m.col_idx, m.values.astype(np.float32), x32, use_fma=True)
@@ -202,12 +244,14 @@ def test_reordered_product_equals_original(oracle):
 # ---------------------------------------------------------------------------------------
 # SpMM
 # ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("bits", [16, 32])
 @pytest.mark.parametrize("k", [1, 3, 8, 32, 64])
 @pytest.mark.parametrize("dtype", [np.float64, np.float32])
-def test_spmm_parity(oracle, k, dtype):
+def test_spmm_parity(oracle, k, dtype, bits):
     m, _ = workloads.mixed(8, k=1)
     X = np.random.default_rng(k).uniform(-1, 1, (m.n, k)).astype(dtype)
-    A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values, precision=capi.SPMV_PREC_DUAL)
+    A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values, precision=capi.SPMV_PREC_DUAL,
+                    index_bits=bits)
     Xd = dev(X)
     Yd = torch.empty_like(Xd)
     A.apply_multi(Xd, Yd)
@@ -225,11 +269,15 @@ def test_spmm_parity(oracle, k, dtype):
 # ---------------------------------------------------------------------------------------
 # full size: the 6M-cell Dirichlet mesh in the benchmark's launch configuration
 # ---------------------------------------------------------------------------------------
-@pytest.mark.parametrize("reorder", [capi.SPMV_REORDER_NONE, capi.SPMV_REORDER_RCM])
-def test_c2_full_size_parity(oracle, reorder):
+@pytest.mark.parametrize("reorder,bits", [(capi.SPMV_REORDER_NONE, 0),
+                                          (capi.SPMV_REORDER_RCM, 16),
+                                          (capi.SPMV_REORDER_RCM, 32)])
+def test_c2_full_size_parity(oracle, reorder, bits):
     m, x = workloads.c2()
     A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values, reorder=reorder,
-                    precision=capi.SPMV_PREC_DUAL)
+                    precision=capi.SPMV_PREC_DUAL, index_bits=bits)
+    if bits:
+        assert A.info()["index_bits"] == bits
     xd = dev(x)
     xi = torch.empty_like(xd)
     A.permute(0, xd, xi)
