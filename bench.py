@@ -33,7 +33,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "SpMV effective GB/s (% HBM peak) FP64 vs mixed; served CG solves/s, p99"
 WORKLOAD = "kuhn-tet 100^3 FV Laplacian, Dirichlet, 6,000,000 rows, 29,880,000 nnz, RCM order"
-FLUSH_BYTES = 512 << 20  # 256 MB written + 256 MB read between timed steps
+FLUSH_BYTES = 512 << 20
+VARIANTS = {0: "auto", 1: "spmv_csr", 2: "spmv_sell", 3: "spmv_sell_window"}  # 256 MB written + 256 MB read between timed steps
 
 
 def spmv_bytes(n, nnz, f32=False):
@@ -247,9 +248,12 @@ def run_gpu(args):
     nbytes = spmv_bytes(n, nnz)
     stream = torch.cuda.Stream(device=dev)
     t_create = time.perf_counter()
+    variant = {"auto": capi.SPMV_VARIANT_AUTO, "sell": capi.SPMV_VARIANT_SELL,
+               "csr": capi.SPMV_VARIANT_CSR, "window": capi.SPMV_VARIANT_SELL_WINDOW}[args.variant]
     A = capi.Matrix(n, m.row_ptr, m.col_idx, m.values, stream=stream,
                     reorder=capi.SPMV_REORDER_RCM, precision=capi.SPMV_PREC_DUAL,
-                    slice_height=args.slice_height)
+                    slice_height=args.slice_height, autotune=int(args.autotune),
+                    variant=variant, index_bits=args.index_bits)
     t_create = time.perf_counter() - t_create
     info = A.info()
     xd = torch.from_numpy(x).to(dev)
@@ -258,6 +262,9 @@ def run_gpu(args):
     A.permute(0, xd, xi, stream)
     flush = torch.zeros(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     fn = lambda: A.apply(xi, yi, stream)  # noqa: E731
+    if args.profile and args.f32:
+        x32, y32 = xi.float(), torch.empty(n, dtype=torch.float32, device=dev)
+        fn = lambda: A.apply_f32(x32, y32, stream)  # noqa: E731
 
     for _ in range(max(3, args.warmup)):
         fn()
@@ -337,7 +344,9 @@ def run_gpu(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": n, "nnz": nnz, "format": "sliced ELLPACK",
-                   "slice_height": info["slice_height"], "reorder": "rcm",
+                   "slice_height": info["slice_height"], "block": info["block"],
+                   "variant": VARIANTS[info["variant"]], "index_bits": info["index_bits"],
+                   "autotuned": bool(args.autotune), "reorder": "rcm",
                    "bandwidth": info["bandwidth"], "max_slice_span": info["max_slice_span"],
                    "algorithmic_bytes_per_step": nbytes, "l2": "flushed between steps (256 MB write, then 256 MB read)",
                    "create_s": round(t_create, 3), "wall_s_timed_region": round(wall, 4),
@@ -350,8 +359,10 @@ def run_gpu(args):
         "roofline": {"bound": "hbm", "achieved": nbytes / avg_launch_s / 1e9, "peak": peak,
                      "unit": "GB/s", "frac": nbytes / avg_launch_s / 1e9 / peak,
                      "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)",
-                     "kernel": "spmv_sell<double,R>",
-                     "traffic": traffic_from_profile("spmv_sell_f64_c2_rcm")},
+                     "kernel": VARIANTS[info["variant"]],
+                     "traffic": traffic_from_profile(
+                         "%s_f64_c2_rcm_i%d_s%d" % (VARIANTS[info["variant"]], info["index_bits"],
+                                                    info["slice_height"]))},
     }
     line.update(extra)
     if rank == 0 and not args.quick and args.serve_requests > 0:
@@ -371,30 +382,48 @@ def secondary(args, torch, capi, workloads, m, x, A, xi, stream, flush, dev):
     out = {}
     n, nnz = m.n, m.nnz
     K = max(10, min(args.steps, 100))
-    # FP32 product of the same handle (the mixed-precision inner SpMV)
-    x32 = xi.float()
-    y32 = torch.empty_like(x32)
-    t = time_kernel(torch, lambda: A.apply_f32(x32, y32, stream), K, flush, stream)
-    b32 = spmv_bytes(n, nnz, f32=True)
-    out["fp32_spmv"] = {"value": b32 / (sum(t) / len(t) / 1e3) / 1e9, "unit": "GB/s",
-                        "ms": sum(t) / len(t), "algorithmic_bytes": b32}
+    nb64 = spmv_bytes(n, nnz)
+    nb32 = spmv_bytes(n, nnz, f32=True)
+
+    def timed(handle, f32=False, csr=False, xin=None):
+        xv = xin if xin is not None else xi
+        if f32:
+            xv = xv.float()
+        yv = torch.empty_like(xv)
+        if f32:
+            fn = lambda: handle.apply_f32(xv, yv, stream)  # noqa: E731
+        elif csr:
+            fn = lambda: handle.apply_csr(xv, yv, stream)  # noqa: E731
+        else:
+            fn = lambda: handle.apply(xv, yv, stream)  # noqa: E731
+        t = time_kernel(torch, fn, K, flush, stream)
+        ms = sum(t) / len(t)
+        nb = nb32 if f32 else nb64
+        return {"value": nb / (ms / 1e3) / 1e9, "unit": "GB/s", "ms": ms}
+
+    # FP32 product (the mixed-precision inner SpMV) of the headline handle
+    out["fp32_spmv"] = dict(timed(A, f32=True), algorithmic_bytes=nb32)
     # the naive CSR kernel (Sec. 4.3 baseline) on the same order
-    yy = torch.empty_like(xi)
-    t = time_kernel(torch, lambda: A.apply_csr(xi, yy, stream), K, flush, stream)
-    nb = spmv_bytes(n, nnz)
-    out["naive_csr_rcm"] = {"value": nb / (sum(t) / len(t) / 1e3) / 1e9, "unit": "GB/s",
-                            "ms": sum(t) / len(t)}
-    # random order (no reordering): sliced and naive
+    out["naive_csr_rcm"] = timed(A, csr=True)
+    # explicit variants of the RCM-ordered matrix (ablation of Sec. 5.1's two ideas)
+    for name, kw in [("sell_int32_cols", dict(index_bits=32)),
+                     ("sell_int16_cols", dict(index_bits=16)),
+                     ("window_int16_cols", dict(index_bits=16,
+                                                variant=capi.SPMV_VARIANT_SELL_WINDOW))]:
+        H = capi.Matrix(n, m.row_ptr, m.col_idx, m.values, stream=stream,
+                        reorder=capi.SPMV_REORDER_RCM, precision=capi.SPMV_PREC_DUAL,
+                        slice_height=64, **kw)
+        hx = torch.empty_like(xi)
+        H.permute(0, torch.from_numpy(x).to(dev), hx, stream)
+        out[name] = {"fp64": timed(H, xin=hx), "fp32": timed(H, f32=True, xin=hx),
+                     "index_bits": H.info()["index_bits"]}
+        H.close()
+    # random order (no reordering): sliced and naive -- the GPU analogue of Table 2's ordering
     R = capi.Matrix(n, m.row_ptr, m.col_idx, m.values, stream=stream,
                     slice_height=args.slice_height)
     xr = torch.from_numpy(x).to(dev)
-    yr = torch.empty_like(xr)
-    t = time_kernel(torch, lambda: R.apply(xr, yr, stream), K, flush, stream)
-    out["sell_random_order"] = {"value": nb / (sum(t) / len(t) / 1e3) / 1e9, "unit": "GB/s",
-                                "ms": sum(t) / len(t)}
-    t = time_kernel(torch, lambda: R.apply_csr(xr, yr, stream), K, flush, stream)
-    out["naive_csr_random_order"] = {"value": nb / (sum(t) / len(t) / 1e3) / 1e9,
-                                     "unit": "GB/s", "ms": sum(t) / len(t)}
+    out["sell_random_order"] = timed(R, xin=xr)
+    out["naive_csr_random_order"] = timed(R, csr=True, xin=xr)
     R.close()
     out.update(cg_results(torch, capi, m, x, A, xi, dev))
     out.update(spmm_results(args, torch, capi, workloads, flush, stream, dev))
@@ -551,8 +580,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--slice-height", type=int, default=64)
+    ap.add_argument("--autotune", type=int, default=1,
+                    help="1: the headline handle picks S, CTA size and variant by timing")
     ap.add_argument("--quick", action="store_true", help="headline only, no secondary results")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--variant", default="auto", choices=["auto", "sell", "csr", "window"],
+                    help="kernel variant of the headline handle (auto: default / autotuned)")
+    ap.add_argument("--index-bits", type=int, default=0, choices=[0, 16, 32])
+    ap.add_argument("--f32", action="store_true",
+                    help="with --profile: time the FP32 product of the handle instead")
     ap.add_argument("--profile-cg", type=int, default=0,
                     help="with --profile: also run CG solves capped at this many iterations")
     ap.add_argument("--serve-requests", type=int, default=48)

@@ -3,7 +3,8 @@
 // warm-up launches).  Each slice height needs its own sliced-ELLPACK arrays, so the arrays are
 // rebuilt per candidate and finally for the winner.  Candidates: S in {32, 64, 128, 256}
 // (S = 512 of the FPGA design is a pipelining depth, Sec. 6.1, and has no GPU meaning),
-// CTA sizes {128, 256, 512}, and the naive CSR kernel (FP64 handles).
+// CTA sizes {128, 256, 512}, the shared-memory window variant, and the naive CSR kernel
+// (FP64 handles).
 #include <algorithm>
 #include <vector>
 
@@ -69,6 +70,19 @@ spmv_status_t autotune_matrix(spmv_matrix_t A, cudaStream_t st) {
                 best_variant = SPMV_VARIANT_SELL;
             }
         }
+        if (s != SPMV_OK) break;
+        if (user_variant == SPMV_VARIANT_AUTO || user_variant == SPMV_VARIANT_SELL_WINDOW) {
+            // shared-memory window of x (one 1024-thread CTA per SM)
+            A->variant = SPMV_VARIANT_SELL_WINDOW;
+            float ms;
+            s = time_launch(A, x, y, st, e0, e1, &ms);
+            if (s != SPMV_OK) break;
+            if (ms < best) {
+                best = ms;
+                best_S = S;
+                best_variant = SPMV_VARIANT_SELL_WINDOW;
+            }
+        }
     }
     if (s == SPMV_OK && A->has64() && user_variant == SPMV_VARIANT_AUTO) {
         A->variant = SPMV_VARIANT_CSR;
@@ -82,7 +96,10 @@ spmv_status_t autotune_matrix(spmv_matrix_t A, cudaStream_t st) {
     if (s == SPMV_OK && best_S != A->S) s = build_sell(A, best_S, st);
     A->block = best_block;
     if (user_variant == SPMV_VARIANT_AUTO) A->variant = best_variant;
-    else A->variant = (user_variant == SPMV_VARIANT_CSR) ? SPMV_VARIANT_CSR : SPMV_VARIANT_SELL;
+    else A->variant = user_variant;
+    A->window_words = A->variant == SPMV_VARIANT_SELL_WINDOW
+                          ? window_capacity_words(A->has64() ? 8 : 4)
+                          : 0;
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (x) cudaFreeAsync(x, st);

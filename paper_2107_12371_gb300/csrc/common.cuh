@@ -159,7 +159,9 @@ spmv_status_t launch_spmm64(spmv_matrix_t A, int k, const double *X, double *Y, 
 spmv_status_t launch_spmm32(spmv_matrix_t A, int k, const float *X, float *Y, cudaStream_t st);
 spmv_status_t launch_permute(spmv_matrix_t A, int direction, int elem_bytes, const void *in,
                              void *out, cudaStream_t st);
-int window_capacity_words(int block);
+int window_capacity_words(int elem_bytes);
+spmv_status_t launch_window64(spmv_matrix_t A, const double *x, double *y, cudaStream_t st);
+spmv_status_t launch_window32(spmv_matrix_t A, const float *x, float *y, cudaStream_t st);
 spmv_status_t choose_variant(spmv_matrix_t A, cudaStream_t st);
 
 // device scan utilities (scan.cu): exclusive prefix sum of n int64 values in place; the

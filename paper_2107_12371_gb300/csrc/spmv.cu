@@ -218,10 +218,12 @@ spmv_status_t launch_spmm(spmv_matrix_t A, int k, const T *val, const T *X, T *Y
 
 spmv_status_t launch_spmv64(spmv_matrix_t A, const double *x, double *y, cudaStream_t st) {
     if (A->variant == SPMV_VARIANT_CSR) return launch_spmv_csr64(A, x, y, st);
+    if (A->variant == SPMV_VARIANT_SELL_WINDOW) return launch_window64(A, x, y, st);
     return launch_sell<double>(A, A->sell_val.p, x, y, st);
 }
 
 spmv_status_t launch_spmv32(spmv_matrix_t A, const float *x, float *y, cudaStream_t st) {
+    if (A->variant == SPMV_VARIANT_SELL_WINDOW) return launch_window32(A, x, y, st);
     return launch_sell<float>(A, A->sell_val32.p, x, y, st);
 }
 
@@ -259,13 +261,11 @@ spmv_status_t launch_permute(spmv_matrix_t A, int direction, int elem_bytes, con
     return SPMV_OK;
 }
 
-int window_capacity_words(int) { return 0; }
-
 spmv_status_t choose_variant(spmv_matrix_t A, cudaStream_t) {
-    if (A->opt.variant == SPMV_VARIANT_AUTO || A->opt.variant == SPMV_VARIANT_SELL_WINDOW)
-        A->variant = SPMV_VARIANT_SELL;
-    else
-        A->variant = A->opt.variant;
+    A->variant = A->opt.variant == SPMV_VARIANT_AUTO ? SPMV_VARIANT_SELL : A->opt.variant;
+    A->window_words = A->variant == SPMV_VARIANT_SELL_WINDOW
+                          ? window_capacity_words(A->has64() ? 8 : 4)
+                          : 0;
     return SPMV_OK;
 }
 

@@ -117,6 +117,34 @@ def test_autotuned_handle_parity(oracle, precision):
     assert np.array_equal(sp, osp) and np.array_equal(col, ocol)
 
 
+@pytest.mark.parametrize("reorder", [capi.SPMV_REORDER_NONE, capi.SPMV_REORDER_RCM])
+@pytest.mark.parametrize("bits", [16, 32])
+@pytest.mark.parametrize("S", [32, 64, 256])
+def test_window_variant_parity(oracle, S, bits, reorder):
+    """Sec. 5.1 circular x window in shared memory: bit-identical to the oracle whether the
+    rounds fit the window (RCM order) or fall back to global gathers (random order, FP64)."""
+    m, x = workloads.c1()
+    A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values, slice_height=S, index_bits=bits,
+                    variant=capi.SPMV_VARIANT_SELL_WINDOW, precision=capi.SPMV_PREC_DUAL,
+                    reorder=reorder)
+    info = A.info()
+    assert info["variant"] == capi.SPMV_VARIANT_SELL_WINDOW and info["window_words"] > 0
+    rp, ci, v = capi.spmv_export_csr(A.handle, m.n, m.nnz)
+    mi = meshgen.CsrMatrix(m.n, rp, ci, v)
+    xi = x[A.permutation()]
+    check_fp64(mi, xi, gpu_spmv(A, xi), oracle)
+    x32 = xi.astype(np.float32)
+    ref = oracle.spmv_f32(rp, ci, v.astype(np.float32), x32, use_fma=True)
+    assert np.array_equal(gpu_spmv(A, x32, f32=True), ref)
+
+
+def test_window_variant_wide_and_ragged(oracle):
+    m = ragged_matrix(20000, 11, max_len=60)
+    x = np.random.default_rng(12).uniform(-1, 1, m.n)
+    A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values, variant=capi.SPMV_VARIANT_SELL_WINDOW)
+    check_fp64(m, x, gpu_spmv(A, x), oracle)
+
+
 def test_c1_naive_csr_parity(oracle):
     m, x = workloads.c1()
     A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values)
