@@ -253,7 +253,7 @@ def run_gpu(args):
     A = capi.Matrix(n, m.row_ptr, m.col_idx, m.values, stream=stream,
                     reorder=capi.SPMV_REORDER_RCM, precision=capi.SPMV_PREC_DUAL,
                     slice_height=args.slice_height, autotune=int(args.autotune),
-                    variant=variant, index_bits=args.index_bits)
+                    variant=variant, index_bits=args.index_bits, block=args.block)
     t_create = time.perf_counter() - t_create
     info = A.info()
     xd = torch.from_numpy(x).to(dev)
@@ -580,6 +580,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--slice-height", type=int, default=64)
+    ap.add_argument("--block", type=int, default=256, help="CTA size of the SpMV kernels")
     ap.add_argument("--autotune", type=int, default=1,
                     help="1: the headline handle picks S, CTA size and variant by timing")
     ap.add_argument("--quick", action="store_true", help="headline only, no secondary results")

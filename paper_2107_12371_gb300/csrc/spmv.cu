@@ -21,9 +21,10 @@ namespace gb {
 namespace {
 
 template <typename T, int R, int L, int U, typename ColT>
-__global__ void __launch_bounds__(1024)
-spmv_sell(int32_t n, int32_t n_slices, const int64_t *__restrict__ sp, ColT cols,
-          const T *__restrict__ val, const T *__restrict__ x, T *__restrict__ y) {
+__device__ __forceinline__ void spmv_sell_body(int32_t n, int32_t n_slices,
+                                               const int64_t *__restrict__ sp, ColT cols,
+                                               const T *__restrict__ val,
+                                               const T *__restrict__ x, T *__restrict__ y) {
     // L lanes per slice, R rows per lane: S = L R rows per slice
     constexpr int S = L * R;
     const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -69,6 +70,23 @@ spmv_sell(int32_t n, int32_t n_slices, const int64_t *__restrict__ sp, ColT cols
             if (c[i] >= 0) acc[i] = fma_t(v[i], ld_x(x + c[i]), acc[i]);
     }
     store_rows<T, R>(y, slice * S + (int64_t)lane * R, n, acc);
+}
+
+template <typename T, int R, int L, int U, typename ColT>
+__global__ void __launch_bounds__(1024)
+spmv_sell(int32_t n, int32_t n_slices, const int64_t *__restrict__ sp, ColT cols,
+          const T *__restrict__ val, const T *__restrict__ x, T *__restrict__ y) {
+    spmv_sell_body<T, R, L, U, ColT>(n, n_slices, sp, cols, val, x, y);
+}
+
+// FP64 with one or two rows per lane, capped at 32 registers (2 x 1024 threads per SM): a
+// full SM of warps keeps enough loads in flight to stream HBM, which the 16-bit decode would
+// otherwise cost in occupancy.
+template <typename T, int R, int L, int U, typename ColT>
+__global__ void __launch_bounds__(1024, 2)
+spmv_sell_occ(int32_t n, int32_t n_slices, const int64_t *__restrict__ sp, ColT cols,
+              const T *__restrict__ val, const T *__restrict__ x, T *__restrict__ y) {
+    spmv_sell_body<T, R, L, U, ColT>(n, n_slices, sp, cols, val, x, y);
 }
 
 // naive CSR baseline (Sec. 4.3): the column index is read first, then x[col] from global
@@ -147,12 +165,17 @@ template <typename T, int R, int L, int U>
 spmv_status_t go_sell(spmv_matrix_t A, const T *val, const T *x, T *y, cudaStream_t st) {
     const int block = A->block;
     const unsigned grid = grid_for((int64_t)A->n_slices * L, block);
-    if (A->index_bits == 16)
-        spmv_sell<T, R, L, U, Cols16><<<grid, block, 0, st>>>(
-            A->n, A->n_slices, A->slice_ptr.p, Cols16{A->sell_col16.p, A->col_start.p}, val, x, y);
-    else
-        spmv_sell<T, R, L, U, Cols32><<<grid, block, 0, st>>>(
-            A->n, A->n_slices, A->slice_ptr.p, Cols32{A->sell_col.p}, val, x, y);
+    auto go = [&](auto c) {
+        using ColT = decltype(c);
+        if constexpr (sizeof(T) == 8 && R <= 2)
+            spmv_sell_occ<T, R, L, U, ColT><<<grid, block, 0, st>>>(A->n, A->n_slices,
+                                                                    A->slice_ptr.p, c, val, x, y);
+        else
+            spmv_sell<T, R, L, U, ColT><<<grid, block, 0, st>>>(A->n, A->n_slices, A->slice_ptr.p,
+                                                                c, val, x, y);
+    };
+    if (A->index_bits == 16) go(Cols16{A->sell_col16.p, A->col_start.p});
+    else go(Cols32{A->sell_col.p});
     GB_LAUNCHED();
     return SPMV_OK;
 }
