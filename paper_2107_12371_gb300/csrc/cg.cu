@@ -206,16 +206,22 @@ __global__ void add_iters(CgScalars *inner, int *total) { *total += inner->iters
 
 }  // namespace
 
-// grid of the CG sweeps: a fixed multiple of the SM count (the persistent kernel uses the
-// same grid), so the reduction order is fixed and both paths give identical results
-int cg_grid() { return device_facts().sm_count * kCgCtasPerSm; }
+// Grid of the CG sweeps of a matrix with n rows: about 4,096 rows per CTA, at most
+// kCgCtasPerSm CTAs per SM (the persistent kernel uses the same grid).  It depends only on n
+// and the device, so the reduction order is fixed per handle and both paths give identical
+// results; small systems use few CTAs and leave the GPU to concurrent solves.
+int cg_grid(int32_t n) {
+    const int cap = device_facts().sm_count * kCgCtasPerSm;
+    const int64_t want = ((int64_t)n + 4095) / 4096;
+    return (int)(want < 1 ? 1 : (want > cap ? cap : want));
+}
 
 spmv_status_t ensure_cg_work(spmv_matrix_t A, bool mixed, cudaStream_t st) {
     CgWork &w = A->cg;
     size_t *t = &A->bytes;
     const size_t n = (size_t)A->n;
     if (!w.ready) {
-        const int G = cg_grid();
+        const int G = cg_grid(A->n);
         w.part_len = G;
         GB_TRY(w.part.alloc((size_t)G * kMaxParts * 2, t));
         GB_TRY(w.scal.alloc(2 * ((sizeof(CgScalars) + 7) / 8), t));
@@ -263,7 +269,7 @@ static spmv_status_t with_cols(spmv_matrix_t A, F &&f) {
 // enqueue `iters` FP64 iterations (3 kernels each)
 static spmv_status_t enqueue_cg64(spmv_matrix_t A, int iters, cudaStream_t st) {
     CgWork &w = A->cg;
-    const int G = cg_grid();
+    const int G = cg_grid(A->n);
     CgScalars *sc = outer_scalars(A);
     return with_cols(A, [&](auto cols) -> spmv_status_t {
         using ColT = decltype(cols);
@@ -285,7 +291,7 @@ static spmv_status_t enqueue_cg64(spmv_matrix_t A, int iters, cudaStream_t st) {
 
 static spmv_status_t enqueue_cg32(spmv_matrix_t A, int iters, cudaStream_t st) {
     CgWork &w = A->cg;
-    const int G = cg_grid();
+    const int G = cg_grid(A->n);
     CgScalars *sc = inner_scalars(A);
     return with_cols(A, [&](auto cols) -> spmv_status_t {
         using ColT = decltype(cols);
@@ -309,7 +315,7 @@ static spmv_status_t enqueue_cg32(spmv_matrix_t A, int iters, cudaStream_t st) {
 static spmv_status_t enqueue_residual64(spmv_matrix_t A, const double *b, bool x_zero,
                                         bool want_p, cudaStream_t st) {
     CgWork &w = A->cg;
-    const int G = cg_grid();
+    const int G = cg_grid(A->n);
     return with_cols(A, [&](auto cols) -> spmv_status_t {
         using ColT = decltype(cols);
         return with_shape(A->S, false, [&](auto rt, auto lt) -> spmv_status_t {
@@ -436,7 +442,7 @@ static spmv_status_t solve_mixed(spmv_matrix_t A, const double *b, const cg_opti
                                  cg_result_t *res, cudaStream_t st, Clock::time_point t0) {
     CgWork &w = A->cg;
     const int batch = o.check_every > 0 ? o.check_every : 16;
-    const int G = cg_grid();
+    const int G = cg_grid(A->n);
     CgScalars *so = outer_scalars(A);
     CgScalars *si = inner_scalars(A);
     int *d_total = w.flags.p + 4;

@@ -10,9 +10,9 @@
 namespace gb {
 
 constexpr int kCgBlock = 256;
-constexpr int kCgCtasPerSm = 4;  // CTAs per SM of every CG sweep (graph and persistent)
+constexpr int kCgCtasPerSm = 4;  // at most this many CTAs per SM in a CG sweep
 
-int cg_grid();
+int cg_grid(int32_t n);
 
 // Sum over the CTA in a fixed tree; the total is left in every lane of warp 0.
 template <int NV>

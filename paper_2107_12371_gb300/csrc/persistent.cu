@@ -179,7 +179,7 @@ spmv_status_t cg_persistent64(spmv_matrix_t A, const cg_options_t &o, CgScalars 
             GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCgBlock, 0));
             // the grid must be co-resident and equal to the graph path's grid
             if (per_sm < kCgCtasPerSm) return SPMV_ERR_UNSUPPORTED;
-            w.pers_grid = cg_grid();
+            w.pers_grid = cg_grid(A->n);
             const long long budget = o.timeout_s > 0 ? (long long)(o.timeout_s * 1e9) : 0;
             GB_CUDA(cudaMemcpyAsync(&sc->budget_ns, &budget, sizeof(budget),
                                     cudaMemcpyHostToDevice, st));
