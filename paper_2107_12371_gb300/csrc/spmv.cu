@@ -11,9 +11,6 @@
 //   columns) as 16-bit offsets from the slice's col_start (Sec. 5.1), 10 instead of 12 bytes
 //   per FP64 non-zero.
 // spmv_csr: the naive baseline of Sec. 4.3, thread per CSR row.
-// spmm_sell<T, G, C>: Y = A X for row-major X, G lanes per row, each lane C columns; every
-//   gathered row of X (k contiguous values) is read once per matrix entry and used for all k
-//   columns.
 #include "common.cuh"
 #include "ptx.cuh"
 
@@ -102,49 +99,6 @@ spmv_csr(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ 
     y[i] = acc;
 }
 
-// SpMM: G lanes per row (G divides 32), lane owns columns g, g + G, ... (C of them)
-template <typename T, int G, int C, typename ColT>
-__global__ void __launch_bounds__(256)
-spmm_sell(int32_t n, int32_t S, int32_t n_slices, int k, const int64_t *__restrict__ sp,
-          ColT cols, const T *__restrict__ val, const T *__restrict__ X, T *__restrict__ Y) {
-    constexpr int RPW = 32 / G;  // rows per warp step
-    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    const int sub = lane / G, g = lane % G;
-    const int64_t rows_total = (int64_t)n_slices * S;
-    const int64_t row = gw * RPW + sub;
-    if (row >= rows_total) return;
-    const int64_t slice = row / S;
-    const int64_t r = row - slice * S;
-    const int64_t base = sp[slice];
-    const int w = (int)((sp[slice + 1] - base) / S);
-    const int32_t cbase = cols.base(slice);
-    const uint64_t pol = policy_evict_first();
-    T acc[C];
-#pragma unroll
-    for (int j = 0; j < C; ++j) acc[j] = T(0);
-    for (int t = 0; t < w; ++t) {
-        T a[1];
-        int32_t c[1];
-        ld_stream(val + base + (int64_t)t * S + r, pol, a);
-        cols.template load<1>(base + (int64_t)t * S + r, slice, pol, cbase, c);
-        if (c[0] < 0) continue;
-        const T *xr = X + (int64_t)c[0] * k;
-#pragma unroll
-        for (int j = 0; j < C; ++j) {
-            const int cc = g + j * G;
-            if (cc < k) acc[j] = fma_t(a[0], ld_x(xr + cc), acc[j]);
-        }
-    }
-    if (row < n) {
-#pragma unroll
-        for (int j = 0; j < C; ++j) {
-            const int cc = g + j * G;
-            if (cc < k) Y[row * k + cc] = acc[j];
-        }
-    }
-}
-
 template <typename T>
 __global__ void permute_kernel(int32_t n, int direction, const int32_t *__restrict__ perm,
                                const T *__restrict__ in, T *__restrict__ out) {
@@ -201,42 +155,6 @@ spmv_status_t launch_sell(spmv_matrix_t A, const T *val, const T *x, T *y, cudaS
     return SPMV_ERR_INVALID_ARG;
 }
 
-template <typename T>
-spmv_status_t launch_spmm(spmv_matrix_t A, int k, const T *val, const T *X, T *Y,
-                          cudaStream_t st) {
-    if (A->n == 0) return SPMV_OK;
-    const int block = 256;
-    const int64_t rows_total = (int64_t)A->n_slices * A->S;
-    auto go = [&](auto gtag, auto ctag) -> spmv_status_t {
-        constexpr int G = decltype(gtag)::value;
-        constexpr int C = decltype(ctag)::value;
-        const int64_t warps = (rows_total + (32 / G) - 1) / (32 / G);
-        const unsigned grid = grid_for(warps * 32, block);
-        if (A->index_bits == 16)
-            spmm_sell<T, G, C, Cols16><<<grid, block, 0, st>>>(
-                A->n, A->S, A->n_slices, k, A->slice_ptr.p, Cols16{A->sell_col16.p, A->col_start.p},
-                val, X, Y);
-        else
-            spmm_sell<T, G, C, Cols32><<<grid, block, 0, st>>>(
-                A->n, A->S, A->n_slices, k, A->slice_ptr.p, Cols32{A->sell_col.p}, val, X, Y);
-        GB_LAUNCHED();
-        return SPMV_OK;
-    };
-    using I1 = std::integral_constant<int, 1>;
-    using I2 = std::integral_constant<int, 2>;
-    using I4 = std::integral_constant<int, 4>;
-    using I8 = std::integral_constant<int, 8>;
-    using I16 = std::integral_constant<int, 16>;
-    using I32 = std::integral_constant<int, 32>;
-    if (k <= 1) return go(I1{}, I1{});
-    if (k <= 2) return go(I2{}, I1{});
-    if (k <= 4) return go(I4{}, I1{});
-    if (k <= 8) return go(I8{}, I1{});
-    if (k <= 16) return go(I16{}, I1{});
-    if (k <= 32) return go(I32{}, I1{});
-    return go(I32{}, I2{});
-}
-
 }  // namespace
 
 spmv_status_t launch_spmv64(spmv_matrix_t A, const double *x, double *y, cudaStream_t st) {
@@ -256,14 +174,6 @@ spmv_status_t launch_spmv_csr64(spmv_matrix_t A, const double *x, double *y, cud
                                                           x, y);
     GB_LAUNCHED();
     return SPMV_OK;
-}
-
-spmv_status_t launch_spmm64(spmv_matrix_t A, int k, const double *X, double *Y, cudaStream_t st) {
-    return launch_spmm<double>(A, k, A->sell_val.p, X, Y, st);
-}
-
-spmv_status_t launch_spmm32(spmv_matrix_t A, int k, const float *X, float *Y, cudaStream_t st) {
-    return launch_spmm<float>(A, k, A->sell_val32.p, X, Y, st);
 }
 
 spmv_status_t launch_permute(spmv_matrix_t A, int direction, int elem_bytes, const void *in,
