@@ -597,7 +597,7 @@ def main():
     ap.add_argument("--profile-cg", type=int, default=0,
                     help="with --profile: also run CG solves capped at this many iterations")
     ap.add_argument("--serve-requests", type=int, default=48)
-    ap.add_argument("--serve-slots", type=int, default=16)
+    ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--profile", action="store_true",
                     help="timed SpMV loop only (for ncu launch lists and captures)")
     args = ap.parse_args()

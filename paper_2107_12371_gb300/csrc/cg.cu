@@ -206,13 +206,13 @@ __global__ void add_iters(CgScalars *inner, int *total) { *total += inner->iters
 
 }  // namespace
 
-// Grid of the CG sweeps of a matrix with n rows: about 4,096 rows per CTA, at most
-// kCgCtasPerSm CTAs per SM (the persistent kernel uses the same grid).  It depends only on n
-// and the device, so the reduction order is fixed per handle and both paths give identical
-// results; small systems use few CTAs and leave the GPU to concurrent solves.
+// Grid of the CG sweeps of a matrix with n rows: about 1,024 rows (4 per thread) per CTA, at
+// most kCgCtasPerSm CTAs per SM (the persistent kernel uses the same grid).  It depends only
+// on n and the device, so the reduction order is fixed per handle and both paths give
+// identical results; small systems use fewer CTAs and leave room for concurrent solves.
 int cg_grid(int32_t n) {
     const int cap = device_facts().sm_count * kCgCtasPerSm;
-    const int64_t want = ((int64_t)n + 4095) / 4096;
+    const int64_t want = ((int64_t)n + 1023) / 1024;
     return (int)(want < 1 ? 1 : (want > cap ? cap : want));
 }
 

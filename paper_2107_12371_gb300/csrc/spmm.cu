@@ -1,6 +1,6 @@
 // spmm.cu -- multi-right-hand-side products Y = A X (not in the paper).
 //
-// spmm_sell<T, G, C, U>: X and Y row-major (n x k), G lanes per row, each lane C columns;
+// spmm_sell<T, G, C>: X and Y row-major (n x k), G lanes per row, each lane C columns;
 // every gathered row of X (k contiguous values) is read once per matrix entry and used for
 // all k columns.  Column c of Y equals the single-vector product of column c bit for bit
 // (same entry order, fused multiply-add from +0.0).
@@ -17,21 +17,24 @@ inline unsigned grid_for(int64_t threads, int block) {
     return (unsigned)(b < 1 ? 1 : b);
 }
 
-// SpMM: G lanes per row (G divides 32), lane owns columns g, g + G, ... (C of them).  The
-// (value, column) pairs of U consecutive steps are loaded before their rows of X are gathered,
-// so every lane keeps U * C gathers in flight instead of one.
-template <typename T, int G, int C, int U, typename ColT>
+// SpMM: G lanes per row (G divides 32, so the RPW = 32 / G rows of a warp lie in one slice and
+// share its width), lane g owns columns g, g + G, ... (C of them).  The lanes of a row first
+// load G of its (value, column) pairs at once, one per lane; the pairs are then broadcast
+// inside the row's lane group by shuffles, four at a time, so each lane issues 4 C gathers of
+// X back to back instead of one dependent load-then-gather round per entry.
+template <typename T, int G, int C, typename ColT>
 __global__ void __launch_bounds__(256)
 spmm_sell(int32_t n, int32_t S, int32_t n_slices, int k, const int64_t *__restrict__ sp,
           ColT cols, const T *__restrict__ val, const T *__restrict__ X, T *__restrict__ Y) {
-    constexpr int RPW = 32 / G;  // rows per warp
+    constexpr int RPW = 32 / G;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     const int sub = lane / G, g = lane % G;
     const int64_t rows_total = (int64_t)n_slices * S;
-    const int64_t row = gw * RPW + sub;
-    if (row >= rows_total) return;
-    const int64_t slice = row / S;
+    const int64_t row0 = gw * RPW;
+    if (row0 >= rows_total) return;  // whole warp: rows_total is a multiple of RPW
+    const int64_t row = row0 + sub;
+    const int64_t slice = row0 / S;
     const int64_t r = row - slice * S;
     const int64_t base = sp[slice];
     const int w = (int)((sp[slice + 1] - base) / S);
@@ -40,40 +43,49 @@ spmm_sell(int32_t n, int32_t S, int32_t n_slices, int k, const int64_t *__restri
     T acc[C];
 #pragma unroll
     for (int j = 0; j < C; ++j) acc[j] = T(0);
-    int t = 0;
-    for (; t + U <= w; t += U) {
-        T a[U][1];
-        int32_t c[U][1];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            ld_stream(val + base + (int64_t)(t + u) * S + r, pol, a[u]);
-            cols.template load<1>(base + (int64_t)(t + u) * S + r, slice, pol, cbase, c[u]);
+    for (int t0 = 0; t0 < w; t0 += G) {
+        T a_l = T(0);
+        int32_t c_l = -1;
+        if (t0 + g < w) {
+            T a1[1];
+            int32_t c1[1];
+            ld_stream(val + base + (int64_t)(t0 + g) * S + r, pol, a1);
+            cols.template load<1>(base + (int64_t)(t0 + g) * S + r, slice, pol, cbase, c1);
+            a_l = a1[0];
+            c_l = c1[0];
         }
-        T xv[U][C];
+        const int cnt = (w - t0) < G ? (w - t0) : G;
+        int tt = 0;
+        for (; tt + 4 <= cnt; tt += 4) {
+            T a[4], xv[4][C];
+            int32_t c[4];
 #pragma unroll
-        for (int u = 0; u < U; ++u)
+            for (int u = 0; u < 4; ++u) {
+                a[u] = __shfl_sync(0xffffffffu, a_l, tt + u, G);
+                c[u] = __shfl_sync(0xffffffffu, c_l, tt + u, G);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int j = 0; j < C; ++j) {
+                    const int cc = g + j * G;
+                    xv[u][j] = (c[u] >= 0 && cc < k) ? ld_x(X + (int64_t)c[u] * k + cc) : T(0);
+                }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int j = 0; j < C; ++j)
+                    if (c[u] >= 0) acc[j] = fma_t(a[u], xv[u][j], acc[j]);
+        }
+        for (; tt < cnt; ++tt) {
+            const T a = __shfl_sync(0xffffffffu, a_l, tt, G);
+            const int32_t c = __shfl_sync(0xffffffffu, c_l, tt, G);
+            if (c < 0) continue;
 #pragma unroll
             for (int j = 0; j < C; ++j) {
                 const int cc = g + j * G;
-                xv[u][j] = (c[u][0] >= 0 && cc < k) ? ld_x(X + (int64_t)c[u][0] * k + cc) : T(0);
+                if (cc < k) acc[j] = fma_t(a, ld_x(X + (int64_t)c * k + cc), acc[j]);
             }
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-#pragma unroll
-            for (int j = 0; j < C; ++j)
-                if (c[u][0] >= 0) acc[j] = fma_t(a[u][0], xv[u][j], acc[j]);
-    }
-    for (; t < w; ++t) {
-        T a[1];
-        int32_t c[1];
-        ld_stream(val + base + (int64_t)t * S + r, pol, a);
-        cols.template load<1>(base + (int64_t)t * S + r, slice, pol, cbase, c);
-        if (c[0] < 0) continue;
-        const T *xr = X + (int64_t)c[0] * k;
-#pragma unroll
-        for (int j = 0; j < C; ++j) {
-            const int cc = g + j * G;
-            if (cc < k) acc[j] = fma_t(a[0], ld_x(xr + cc), acc[j]);
         }
     }
     if (row < n) {
@@ -97,11 +109,11 @@ spmv_status_t launch_spmm(spmv_matrix_t A, int k, const T *val, const T *X, T *Y
         const int64_t warps = (rows_total + (32 / G) - 1) / (32 / G);
         const unsigned grid = grid_for(warps * 32, block);
         if (A->index_bits == 16)
-            spmm_sell<T, G, C, 4, Cols16><<<grid, block, 0, st>>>(
+            spmm_sell<T, G, C, Cols16><<<grid, block, 0, st>>>(
                 A->n, A->S, A->n_slices, k, A->slice_ptr.p, Cols16{A->sell_col16.p, A->col_start.p},
                 val, X, Y);
         else
-            spmm_sell<T, G, C, 4, Cols32><<<grid, block, 0, st>>>(
+            spmm_sell<T, G, C, Cols32><<<grid, block, 0, st>>>(
                 A->n, A->S, A->n_slices, k, A->slice_ptr.p, Cols32{A->sell_col.p}, val, X, Y);
         GB_LAUNCHED();
         return SPMV_OK;
