@@ -76,6 +76,10 @@ typedef struct {
     int index_bits;      /* 0 = 16 when every slice spans < 65,535 columns, else 32;
                           * 32 = always int32 columns; 16 = 16-bit where possible.  16-bit
                           * columns are offsets from the slice's col_start (Sec. 5.1). */
+    int sigma;           /* 0 = off; else a power of two in [32, 4096]: after the reordering,
+                          * rows are sorted by decreasing length (stable) inside windows of
+                          * sigma rows, so the slices pad less (the rows are renumbered: use
+                          * spmv_permute / spmv_get_permutation as for a reordering). */
 } spmv_options_t;
 
 /* Fills *opt with the defaults (S = 64, block = 256, AUTO variant, no reordering, FP64,
@@ -138,7 +142,8 @@ spmv_status_t spmv_export_sell(spmv_matrix_t A, int64_t *slice_ptr, int32_t *col
 
 /*
  * spmv_apply -- async.  y = A x (overwrites y) in the internal numbering (Sec. 4.3 / 5.2).
- * x_dev, y_dev: device double[n_rows] (FP64 / DUAL handles); must not overlap.
+ * x_dev, y_dev: device double[n_rows] (FP64 / DUAL handles), 16-byte aligned; must not
+ * overlap.
  * Summation order per row: ascending column, fused multiply-add from +0.0.
  */
 spmv_status_t spmv_apply(spmv_matrix_t A, const double *x_dev, double *y_dev, void *stream);
@@ -152,8 +157,10 @@ spmv_status_t spmv_apply_csr(spmv_matrix_t A, const double *x_dev, double *y_dev
 
 /*
  * spmv_apply_multi -- async.  Y = A X for k right-hand sides, X and Y row-major
- * (n_rows x k, entry (i, c) at i*k + c), device memory, FP64.  1 <= k <= 64.  Each gathered
- * row of X is reused for all k columns.  Column c equals spmv_apply on column c bit for bit.
+ * (n_rows x k, entry (i, c) at i*k + c), device memory, FP64, 16-byte aligned, not
+ * overlapping.  1 <= k <= 64.  Each gathered row of X is reused for all k columns (power-of-two
+ * k are gathered with 16-byte vector loads).  Column c equals spmv_apply on column c bit for
+ * bit.
  */
 spmv_status_t spmv_apply_multi(spmv_matrix_t A, int k, const double *X_dev, double *Y_dev,
                                void *stream);

@@ -62,6 +62,8 @@ def lib():
         L.oracle_spmm_f32.restype = None
         L.oracle_cm_order.argtypes = [_i32, _i32p, _i32p, _int, _int, _i32p]
         L.oracle_cm_order.restype = _int
+        L.oracle_sigma_sort.argtypes = [_i32, _i32p, ctypes.c_void_p, _i32, _i32p]
+        L.oracle_sigma_sort.restype = _int
         L.oracle_permute_csr.argtypes = [_i32, _i32p, _i32p, _f64p, _i32p, _i32p, _i32p, _f64p]
         L.oracle_permute_csr.restype = _int
         L.oracle_sell_slice_ptr.argtypes = [_i32, _i32p, _i32, _i64p]
@@ -130,6 +132,19 @@ def cm_order(row_ptr, col_idx, reverse=True, peripheral=True):
     if rc != 0:
         raise RuntimeError("oracle_cm_order failed: %d" % rc)
     return perm
+
+
+def sigma_sort(row_ptr, sigma, perm_in=None):
+    """Rows (in the order perm_in, default identity) sorted by decreasing length inside windows
+    of sigma positions, ties kept in order; returns perm[new] = old."""
+    rp = np.ascontiguousarray(row_ptr, np.int32)
+    n = rp.size - 1
+    out = np.empty(n, np.int32)
+    pin = None if perm_in is None else np.ascontiguousarray(perm_in, np.int32)
+    rc = lib().oracle_sigma_sort(n, rp, None if pin is None else pin.ctypes.data, int(sigma), out)
+    if rc != 0:
+        raise RuntimeError("oracle_sigma_sort failed: %d" % rc)
+    return out
 
 
 def permute_csr(row_ptr, col_idx, values, perm):

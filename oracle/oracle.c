@@ -237,6 +237,31 @@ int oracle_cm_order(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, i
     return 0;
 }
 
+/* Length sorting inside windows (sliced ELLPACK with sorting scope sigma, ref. MON10 and its  */
+/* SELL-C-sigma refinement): rows are taken in the order perm_in (perm_in[new] = old; NULL =  */
+/* identity); inside each window of sigma consecutive positions they are reordered by         */
+/* decreasing row length, rows of equal length keeping their order.  perm_out[new] = old.     */
+int oracle_sigma_sort(int32_t n, const int32_t *row_ptr, const int32_t *perm_in, int32_t sigma,
+                      int32_t *perm_out)
+{
+    if (n < 0 || sigma < 1) return -1;
+    for (int32_t i = 0; i < n; ++i) perm_out[i] = perm_in ? perm_in[i] : i;
+    for (int32_t w0 = 0; w0 < n; w0 += sigma) {
+        int32_t w1 = w0 + sigma < n ? w0 + sigma : n;
+        for (int32_t a = w0 + 1; a < w1; ++a) { /* stable insertion sort, longest first */
+            int32_t v = perm_out[a];
+            int32_t lv = row_ptr[v + 1] - row_ptr[v];
+            int32_t b = a - 1;
+            while (b >= w0 && row_ptr[perm_out[b] + 1] - row_ptr[perm_out[b]] < lv) {
+                perm_out[b + 1] = perm_out[b];
+                --b;
+            }
+            perm_out[b + 1] = v;
+        }
+    }
+    return 0;
+}
+
 /* Symmetric permutation B = P A P^T with perm[new] = old: row r of B is row perm[r] of A,  */
 /* every column c renumbered to inv[c], then the row sorted by new column (Sec. 4.1: the    */
 /* coefficients are unchanged, only renumbered).                                            */

@@ -37,7 +37,7 @@ class spmv_options_t(ctypes.Structure):
                 ("variant", ctypes.c_int), ("reorder", ctypes.c_int),
                 ("precision", ctypes.c_int), ("autotune", ctypes.c_int),
                 ("peripheral", ctypes.c_int), ("window_words", ctypes.c_int),
-                ("index_bits", ctypes.c_int)]
+                ("index_bits", ctypes.c_int), ("sigma", ctypes.c_int)]
 
 
 class spmv_info_t(ctypes.Structure):

@@ -51,6 +51,8 @@ static spmv_status_t normalize_options(const spmv_options_t *in, spmv_options_t 
     if (o->precision < SPMV_PREC_FP64 || o->precision > SPMV_PREC_DUAL) return SPMV_ERR_INVALID_ARG;
     if (o->window_words < 0) return SPMV_ERR_INVALID_ARG;
     if (o->index_bits != 0 && o->index_bits != 16 && o->index_bits != 32) return SPMV_ERR_INVALID_ARG;
+    if (o->sigma != 0 && (o->sigma < 32 || o->sigma > 4096 || (o->sigma & (o->sigma - 1)) != 0))
+        return SPMV_ERR_INVALID_ARG;
     return SPMV_OK;
 }
 
@@ -75,6 +77,7 @@ spmv_status_t spmv_default_options(spmv_options_t *opt) {
     opt->peripheral = 1;
     opt->window_words = 0;
     opt->index_bits = 0;
+    opt->sigma = 0;
     return SPMV_OK;
 }
 
@@ -263,7 +266,8 @@ spmv_status_t spmv_apply_csr(spmv_matrix_t A, const double *x, double *y, void *
 
 spmv_status_t spmv_apply_multi(spmv_matrix_t A, int k, const double *X, double *Y, void *stream) {
     if (!A || k < 1 || k > 64) return SPMV_ERR_INVALID_ARG;
-    if (A->n > 0 && (!X || !Y || X == Y)) return SPMV_ERR_INVALID_ARG;
+    if (A->n > 0 && (!X || !Y || X == Y || !aligned16(X) || !aligned16(Y)))
+        return SPMV_ERR_INVALID_ARG;
     if (!A->has64()) return SPMV_ERR_UNSUPPORTED;
     return launch_spmm64(A, k, X, Y, (cudaStream_t)stream);
 }
@@ -271,7 +275,8 @@ spmv_status_t spmv_apply_multi(spmv_matrix_t A, int k, const double *X, double *
 spmv_status_t spmv_apply_multi_f32(spmv_matrix_t A, int k, const float *X, float *Y,
                                    void *stream) {
     if (!A || k < 1 || k > 64) return SPMV_ERR_INVALID_ARG;
-    if (A->n > 0 && (!X || !Y || X == Y)) return SPMV_ERR_INVALID_ARG;
+    if (A->n > 0 && (!X || !Y || X == Y || !aligned16(X) || !aligned16(Y)))
+        return SPMV_ERR_INVALID_ARG;
     if (!A->has32()) return SPMV_ERR_UNSUPPORTED;
     return launch_spmm32(A, k, X, Y, (cudaStream_t)stream);
 }

@@ -335,6 +335,49 @@ spmv_status_t cm_order_device(int32_t n, const int32_t *rp, const int32_t *ci, b
 }
 
 // ---------------------------------------------------------------------------------------
+// length sorting inside windows of sigma rows (sliced ELLPACK with a sorting scope, ref.
+// MON10): rows taken in the order perm_in (nullptr = identity) are reordered inside each window
+// by decreasing length, equal lengths keeping their order, so the slices of a window pad less.
+// One CTA per window: bitonic sort of the unique keys (INT_MAX - length, position).
+// ---------------------------------------------------------------------------------------
+__global__ void sigma_sort_kernel(int32_t n, int32_t sigma, const int32_t *rp,
+                                  const int32_t *perm_in, int32_t *perm_out) {
+    extern __shared__ unsigned long long keys[];
+    const int64_t w0 = (int64_t)blockIdx.x * sigma;
+    const int cnt = (int)((n - w0) < sigma ? (n - w0) : sigma);
+    for (int j = threadIdx.x; j < sigma; j += blockDim.x) {
+        if (j < cnt) {
+            const int32_t old = perm_in ? perm_in[w0 + j] : (int32_t)(w0 + j);
+            const uint32_t len = (uint32_t)(rp[old + 1] - rp[old]);
+            keys[j] = ((unsigned long long)(0x7fffffffu - len) << 32) | (uint32_t)j;
+        } else {
+            keys[j] = ~0ull;
+        }
+    }
+    __syncthreads();
+    for (int k = 2; k <= sigma; k <<= 1) {
+        for (int jj = k >> 1; jj > 0; jj >>= 1) {
+            for (int i = threadIdx.x; i < sigma; i += blockDim.x) {
+                const int ixj = i ^ jj;
+                if (ixj > i) {
+                    const bool up = (i & k) == 0;
+                    const unsigned long long a = keys[i], b = keys[ixj];
+                    if ((a > b) == up) {
+                        keys[i] = b;
+                        keys[ixj] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+        const int32_t src = (int32_t)(keys[j] & 0xffffffffull);
+        perm_out[w0 + j] = perm_in ? perm_in[w0 + src] : (int32_t)(w0 + src);
+    }
+}
+
+// ---------------------------------------------------------------------------------------
 // symmetric permutation B = P A P^T (perm[new] = old), rows sorted by new column
 // ---------------------------------------------------------------------------------------
 __global__ void inverse_perm(int32_t n, const int32_t *perm, int32_t *inv) {
@@ -574,11 +617,27 @@ spmv_status_t build_matrix(spmv_matrix_t A, const int32_t *d_rp, const int32_t *
     GB_TRY(A->col.alloc((size_t)nnz, tally));
     GB_TRY(A->val.alloc((size_t)nnz, tally));
 
-    // 2. ordering and symmetric permutation (Sec. 4.1)
-    if (A->opt.reorder != SPMV_REORDER_NONE && n > 0) {
+    // 2. ordering (Sec. 4.1), optional length sorting inside windows, symmetric permutation
+    const bool reorder = A->opt.reorder != SPMV_REORDER_NONE;
+    const int sigma = A->opt.sigma;
+    if ((reorder || sigma > 0) && n > 0) {
         GB_TRY(A->perm.alloc((size_t)n, tally));
-        GB_TRY(cm_order_device(n, d_rp, d_ci, A->opt.reorder == SPMV_REORDER_RCM,
-                               A->opt.peripheral != 0, A->perm.p, st));
+        if (reorder)
+            GB_TRY(cm_order_device(n, d_rp, d_ci, A->opt.reorder == SPMV_REORDER_RCM,
+                                   A->opt.peripheral != 0, A->perm.p, st));
+        if (sigma > 0) {
+            int32_t *tmp = nullptr;
+            GB_CUDA(cudaMallocAsync((void **)&tmp, sizeof(int32_t) * n, st));
+            const unsigned windows = (unsigned)(((int64_t)n + sigma - 1) / sigma);
+            sigma_sort_kernel<<<windows, 1024, sizeof(unsigned long long) * sigma, st>>>(
+                n, sigma, d_rp, reorder ? A->perm.p : nullptr, tmp);
+            spmv_status_t s = cuda_status(cudaGetLastError());
+            if (s == SPMV_OK)
+                s = cuda_status(cudaMemcpyAsync(A->perm.p, tmp, sizeof(int32_t) * n,
+                                                cudaMemcpyDeviceToDevice, st));
+            cudaFreeAsync(tmp, st);
+            if (s != SPMV_OK) return s;
+        }
         int32_t *inv = nullptr;
         int64_t *len = nullptr;
         GB_CUDA(cudaMallocAsync((void **)&inv, sizeof(int32_t) * n, st));

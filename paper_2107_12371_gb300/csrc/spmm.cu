@@ -97,12 +97,155 @@ spmm_sell(int32_t n, int32_t S, int32_t n_slices, int k, const int64_t *__restri
     }
 }
 
+// Vectorised SpMM for k = VW * G: lane g of a row's G lanes owns the VW consecutive columns
+// g VW .. g VW + VW - 1 and gathers them with one VW-wide load (8 or 16 bytes).  Each lane
+// preloads PE / G of its row's (value, column) pairs, so PE = 16 pairs are fetched in one
+// round; they are broadcast by shuffles four at a time.
+template <typename T, int VW>
+struct VecOf;
+template <>
+struct VecOf<double, 1> {
+    static __device__ __forceinline__ void load(const double *p, double (&v)[1]) { v[0] = __ldg(p); }
+    static __device__ __forceinline__ void store(double *p, const double (&v)[1]) { p[0] = v[0]; }
+};
+template <>
+struct VecOf<double, 2> {
+    static __device__ __forceinline__ void load(const double *p, double (&v)[2]) {
+        const double2 t = __ldg(reinterpret_cast<const double2 *>(p));
+        v[0] = t.x;
+        v[1] = t.y;
+    }
+    static __device__ __forceinline__ void store(double *p, const double (&v)[2]) {
+        *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+    }
+};
+template <>
+struct VecOf<float, 2> {
+    static __device__ __forceinline__ void load(const float *p, float (&v)[2]) {
+        const float2 t = __ldg(reinterpret_cast<const float2 *>(p));
+        v[0] = t.x;
+        v[1] = t.y;
+    }
+    static __device__ __forceinline__ void store(float *p, const float (&v)[2]) {
+        *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+    }
+};
+template <>
+struct VecOf<float, 4> {
+    static __device__ __forceinline__ void load(const float *p, float (&v)[4]) {
+        const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+        v[0] = t.x;
+        v[1] = t.y;
+        v[2] = t.z;
+        v[3] = t.w;
+    }
+    static __device__ __forceinline__ void store(float *p, const float (&v)[4]) {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+};
+
+template <typename T, int VW, int G, typename ColT>
+__global__ void __launch_bounds__(256)
+spmm_sell_vec(int32_t n, int32_t S, int32_t n_slices, const int64_t *__restrict__ sp, ColT cols,
+              const T *__restrict__ val, const T *__restrict__ X, T *__restrict__ Y) {
+    constexpr int K = VW * G;
+    constexpr int RPW = 32 / G;
+    constexpr int PE = 16;                      // pairs preloaded per round
+    constexpr int PL = PE / G > 0 ? PE / G : 1;  // pairs per lane per round
+    constexpr int PR = PL * G;                  // pairs per round
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane / G, g = lane % G;
+    const int64_t rows_total = (int64_t)n_slices * S;
+    const int64_t row0 = gw * RPW;
+    if (row0 >= rows_total) return;  // whole warp: rows_total is a multiple of RPW
+    const int64_t row = row0 + sub;
+    const int64_t slice = row0 / S;
+    const int64_t r = row - slice * S;
+    const int64_t base = sp[slice];
+    const int w = (int)((sp[slice + 1] - base) / S);
+    const int32_t cbase = cols.base(slice);
+    const uint64_t pol = policy_evict_first();
+    T acc[VW];
+#pragma unroll
+    for (int j = 0; j < VW; ++j) acc[j] = T(0);
+    for (int t0 = 0; t0 < w; t0 += PR) {
+        T a_l[PL];
+        int32_t c_l[PL];
+#pragma unroll
+        for (int q = 0; q < PL; ++q) {
+            const int t = t0 + q * G + g;
+            a_l[q] = T(0);
+            c_l[q] = -1;
+            if (t < w) {
+                T a1[1];
+                int32_t c1[1];
+                ld_stream(val + base + (int64_t)t * S + r, pol, a1);
+                cols.template load<1>(base + (int64_t)t * S + r, slice, pol, cbase, c1);
+                a_l[q] = a1[0];
+                c_l[q] = c1[0];
+            }
+        }
+        const int cnt = (w - t0) < PR ? (w - t0) : PR;
+#pragma unroll
+        for (int e0 = 0; e0 < PR; e0 += 4) {
+            if (e0 >= cnt) break;
+            T a[4], xv[4][VW];
+            int32_t c[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = e0 + u;  // pair e lives in lane e % G, slot e / G
+                a[u] = __shfl_sync(0xffffffffu, a_l[(e / G) % PL], e % G, G);
+                c[u] = __shfl_sync(0xffffffffu, c_l[(e / G) % PL], e % G, G);
+                if (e >= cnt) c[u] = -1;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (c[u] >= 0) VecOf<T, VW>::load(X + (int64_t)c[u] * K + g * VW, xv[u]);
+                else {
+#pragma unroll
+                    for (int j = 0; j < VW; ++j) xv[u][j] = T(0);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int j = 0; j < VW; ++j)
+                    if (c[u] >= 0) acc[j] = fma_t(a[u], xv[u][j], acc[j]);
+        }
+    }
+    if (row < n) VecOf<T, VW>::store(Y + row * K + g * VW, acc);
+}
+
 template <typename T>
 spmv_status_t launch_spmm(spmv_matrix_t A, int k, const T *val, const T *X, T *Y,
                           cudaStream_t st) {
     if (A->n == 0) return SPMV_OK;
     const int block = 256;
     const int64_t rows_total = (int64_t)A->n_slices * A->S;
+    // vectorised kernel when k is a power of two with k >= 16 / sizeof(T), k <= 64
+    constexpr int VW = sizeof(T) == 8 ? 2 : 4;
+    auto vec = [&](auto gtag) -> spmv_status_t {
+        constexpr int G = decltype(gtag)::value;
+        const int64_t warps = (rows_total + (32 / G) - 1) / (32 / G);
+        const unsigned grid = grid_for(warps * 32, block);
+        if (A->index_bits == 16)
+            spmm_sell_vec<T, VW, G, Cols16><<<grid, block, 0, st>>>(
+                A->n, A->S, A->n_slices, A->slice_ptr.p, Cols16{A->sell_col16.p, A->col_start.p},
+                val, X, Y);
+        else
+            spmm_sell_vec<T, VW, G, Cols32><<<grid, block, 0, st>>>(
+                A->n, A->S, A->n_slices, A->slice_ptr.p, Cols32{A->sell_col.p}, val, X, Y);
+        GB_LAUNCHED();
+        return SPMV_OK;
+    };
+    using std::integral_constant;
+    if (k == VW * 1) return vec(integral_constant<int, 1>{});
+    if (k == VW * 2) return vec(integral_constant<int, 2>{});
+    if (k == VW * 4) return vec(integral_constant<int, 4>{});
+    if (k == VW * 8) return vec(integral_constant<int, 8>{});
+    if (k == VW * 16) return vec(integral_constant<int, 16>{});
+    if (k == VW * 32 && VW * 32 <= 64) return vec(integral_constant<int, 32>{});
     auto go = [&](auto gtag, auto ctag) -> spmv_status_t {
         constexpr int G = decltype(gtag)::value;
         constexpr int C = decltype(ctag)::value;

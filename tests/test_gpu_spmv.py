@@ -238,6 +238,28 @@ def test_gpu_cm_order_hand_worked_graphs(oracle):
             assert list(A.permutation()) == expect
 
 
+@pytest.mark.parametrize("reorder", [capi.SPMV_REORDER_NONE, capi.SPMV_REORDER_RCM])
+@pytest.mark.parametrize("sigma", [64, 1024, 4096])
+def test_sigma_sorted_rows_match_oracle(oracle, sigma, reorder):
+    """Length sorting inside windows of sigma rows: permutation, permuted CSR and sliced
+    ELLPACK bit-exact against the oracle; less padding on the mixed mesh; product unchanged."""
+    m, x = workloads.mixed(10, k=None)
+    A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values, reorder=reorder, sigma=sigma)
+    base = oracle.cm_order(m.row_ptr, m.col_idx) if reorder else None
+    ref = oracle.sigma_sort(m.row_ptr, sigma, perm_in=base)
+    assert np.array_equal(A.permutation(), ref)
+    rp, ci, v = capi.spmv_export_csr(A.handle, m.n, m.nnz)
+    orp, oci, ov = oracle.permute_csr(m.row_ptr, m.col_idx, m.values, ref)
+    assert np.array_equal(rp, orp) and np.array_equal(ci, oci) and np.array_equal(v, ov)
+    sp, col, val, cs, ce = capi.spmv_export_sell(A.handle)
+    osp, ocol, oval = oracle.sell(orp, oci, ov, A.info()["slice_height"])
+    assert np.array_equal(sp, osp) and np.array_equal(col, ocol) and np.array_equal(val, oval)
+    B = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values, reorder=reorder)
+    assert A.info()["sell_entries"] < B.info()["sell_entries"]
+    xi = x[ref]
+    check_fp64(meshgen.CsrMatrix(m.n, rp, ci, v), xi, gpu_spmv(A, xi), oracle)
+
+
 @pytest.mark.parametrize("S", [32, 64, 128, 256])
 def test_sell_and_window_export_match_oracle(oracle, S):
     m, _ = workloads.mixed(6, k=1)
@@ -273,7 +295,7 @@ def test_reordered_product_equals_original(oracle):
 # SpMM
 # ---------------------------------------------------------------------------------------
 @pytest.mark.parametrize("bits", [16, 32])
-@pytest.mark.parametrize("k", [1, 3, 8, 32, 64])
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 8, 16, 32, 64])
 @pytest.mark.parametrize("dtype", [np.float64, np.float32])
 def test_spmm_parity(oracle, k, dtype, bits):
     m, _ = workloads.mixed(8, k=1)

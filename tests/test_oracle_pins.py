@@ -360,6 +360,25 @@ def test_rcm_reduces_bandwidth_and_is_permutation(oracle):
     assert _bandwidth(qrp, qci) == 1
 
 
+def test_sigma_sort_hand_worked_and_invariants(oracle):
+    """Row lengths 2 5 2 3 | 1 4 with windows of 4: longest first, equal lengths in order,
+    windows never mix -> order 1 3 0 2 | 5 4 (worked by hand).  Starting from the reversed
+    order 5 4 3 2 | 1 0 (lengths 4 1 3 2 | 5 2) -> 5 3 2 4 | 1 0."""
+    lens = np.array([2, 5, 2, 3, 1, 4])
+    rp = np.concatenate([[0], np.cumsum(lens)]).astype(np.int32)
+    assert list(oracle.sigma_sort(rp, 4)) == [1, 3, 0, 2, 5, 4]
+    assert list(oracle.sigma_sort(rp, 4, perm_in=[5, 4, 3, 2, 1, 0])) == [5, 3, 2, 4, 1, 0]
+    m, _ = meshgen.mixed_matrix(6, seed=1)
+    base = oracle.cm_order(m.row_ptr, m.col_idx)
+    p = oracle.sigma_sort(m.row_ptr, 64, perm_in=base)
+    assert np.array_equal(np.sort(p), np.arange(m.n))
+    L = np.diff(m.row_ptr)[p]
+    for w0 in range(0, m.n, 64):
+        seg = L[w0:w0 + 64]
+        assert np.all(np.diff(seg) <= 0)
+        assert set(p[w0:w0 + 64]) == set(base[w0:w0 + 64])
+
+
 def test_permute_csr_is_pap_t(oracle):
     m, _ = meshgen.kuhn_tet_matrix(3, seed=1, dirichlet=True)
     perm = np.random.default_rng(4).permutation(m.n).astype(np.int32)
