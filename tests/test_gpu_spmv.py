@@ -255,7 +255,11 @@ def test_sigma_sorted_rows_match_oracle(oracle, sigma, reorder):
     osp, ocol, oval = oracle.sell(orp, oci, ov, A.info()["slice_height"])
     assert np.array_equal(sp, osp) and np.array_equal(col, ocol) and np.array_equal(val, oval)
     B = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values, reorder=reorder)
-    assert A.info()["sell_entries"] < B.info()["sell_entries"]
+    # sorting inside one slice (sigma = S) cannot change that slice's width
+    if sigma > A.info()["slice_height"]:
+        assert A.info()["sell_entries"] < B.info()["sell_entries"]
+    else:
+        assert A.info()["sell_entries"] == B.info()["sell_entries"]
     xi = x[ref]
     check_fp64(meshgen.CsrMatrix(m.n, rp, ci, v), xi, gpu_spmv(A, xi), oracle)
 
