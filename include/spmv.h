@@ -92,9 +92,11 @@ const char *spmv_status_string(spmv_status_t status);
 /*
  * spmv_create -- sync.  Builds a matrix handle from CSR (Sec. 4.2 input; Sec. 4.1 reordering;
  * Sec. 4.2 sliced ELLPACK; Sec. 5.1 per-slice column range).
- *   n_rows == n_cols (square) >= 0; nnz >= 0; row_ptr int32[n_rows+1] with row_ptr[0] = 0 and
- *   row_ptr[n_rows] = nnz; col_idx int32[nnz], strictly increasing inside each row, in
- *   [0, n_cols); values double[nnz].
+ *   n_rows, n_cols >= 0 (rectangular operators such as the divergence and gradient matrices of
+ *   the operator-based formulation, Sec. 2, are allowed when opt->reorder is NONE and
+ *   opt->sigma is 0; reordering and CG need n_rows == n_cols); nnz >= 0; row_ptr
+ *   int32[n_rows+1] with row_ptr[0] = 0 and row_ptr[n_rows] = nnz; col_idx int32[nnz], strictly
+ *   increasing inside each row, in [0, n_cols); values double[nnz].
  *   inputs_on_device: 0 = the three arrays are host pointers, 1 = device pointers.
  *   The arrays are copied; the caller keeps ownership and may free them after return.
  *   opt may be NULL (defaults).  On success *out owns every device buffer of the matrix.
@@ -124,6 +126,7 @@ typedef struct {
     int32_t window_words;    /* shared-memory window capacity (SELL_WINDOW), else 0 */
     size_t device_bytes;     /* device memory owned by the handle                 */
     int32_t index_bits;      /* 32 or 16 (column indices streamed by the kernels) */
+    int32_t n_cols;
 } spmv_info_t;
 spmv_status_t spmv_get_info(spmv_matrix_t A, spmv_info_t *info);
 
@@ -147,6 +150,16 @@ spmv_status_t spmv_export_sell(spmv_matrix_t A, int64_t *slice_ptr, int32_t *col
  * Summation order per row: ascending column, fused multiply-add from +0.0.
  */
 spmv_status_t spmv_apply(spmv_matrix_t A, const double *x_dev, double *y_dev, void *stream);
+
+/* async.  y = alpha (A x) + beta y (the accumulating form of the paper's task signature, whose
+ * result vector is read and written, Sec. 3.2): t = the row sum in column order, then
+ * y_i = fma(alpha, t, beta * y_i), or alpha * t when beta == 0 (y is then not read, so it may
+ * hold NaN).  x: double[n_cols], y: double[n_rows], 16-byte aligned, not overlapping.
+ * FP64 / DUAL handles; the _f32 form takes FP32 vectors and scalars (FP32 / DUAL handles). */
+spmv_status_t spmv_apply_axpby(spmv_matrix_t A, double alpha, const double *x_dev, double beta,
+                               double *y_dev, void *stream);
+spmv_status_t spmv_apply_axpby_f32(spmv_matrix_t A, float alpha, const float *x_dev, float beta,
+                                   float *y_dev, void *stream);
 
 /* async.  y = A32 x with FP32 values, vector and accumulation (FP32 / DUAL handles). */
 spmv_status_t spmv_apply_f32(spmv_matrix_t A, const float *x_dev, float *y_dev, void *stream);
@@ -200,7 +213,8 @@ spmv_status_t cg_default_options(cg_options_t *opt);
  * cg_solve -- sync.  Solves A x = b for SPD A by Jacobi-preconditioned CG (FP64), or with
  * opt->mixed by FP32 inner Jacobi-PCG and FP64 iterative refinement (residual, norms and the
  * update of x in FP64).  b_dev, x_dev: device double[n_rows] in the internal numbering.
- * Requires a non-zero diagonal entry in every row.  Returns NOT_CONVERGED / TIMEOUT with
+ * Requires a square matrix (else INVALID_ARG) with a non-zero diagonal entry in every row.
+ * Returns NOT_CONVERGED / TIMEOUT with
  * x_dev holding the last iterate; result (may be NULL) is filled in every case.
  */
 spmv_status_t cg_solve(spmv_matrix_t A, const double *b_dev, double *x_dev, const cg_options_t *opt,

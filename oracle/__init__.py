@@ -56,6 +56,8 @@ def lib():
         L.oracle_csr_spmv.restype = None
         L.oracle_csr_spmv_f32.argtypes = [_i32, _i32p, _i32p, _f32p, _f32p, _f32p, _int]
         L.oracle_csr_spmv_f32.restype = None
+        L.oracle_csr_spmv_axpby.argtypes = [_i32, _i32p, _i32p, _f64p, _f64, _f64p, _f64, _f64p]
+        L.oracle_csr_spmv_axpby.restype = None
         L.oracle_spmm.argtypes = [_i32, _i32p, _i32p, _f64p, _i32, _f64p, _f64p, _int]
         L.oracle_spmm.restype = None
         L.oracle_spmm_f32.argtypes = [_i32, _i32p, _i32p, _f32p, _i32, _f32p, _f32p, _int]
@@ -94,6 +96,16 @@ def spmv(row_ptr, col_idx, values, x, use_fma=False):
     lib().oracle_csr_spmv(n, rp, ci, np.ascontiguousarray(values, np.float64),
                           np.ascontiguousarray(x, np.float64), y, int(use_fma))
     return y
+
+
+def spmv_axpby(row_ptr, col_idx, values, alpha, x, beta, y):
+    """y = alpha (A x) + beta y (returns a new array; beta == 0 ignores y)."""
+    rp, ci = _csr(row_ptr, col_idx)
+    out = np.array(y, dtype=np.float64, copy=True)
+    lib().oracle_csr_spmv_axpby(rp.size - 1, rp, ci, np.ascontiguousarray(values, np.float64),
+                                float(alpha), np.ascontiguousarray(x, np.float64), float(beta),
+                                out)
+    return out
 
 
 def spmv_f32(row_ptr, col_idx, values32, x32, use_fma=True):

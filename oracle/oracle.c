@@ -44,6 +44,20 @@ void oracle_csr_spmv(int32_t n_rows, const int32_t *row_ptr, const int32_t *col_
     }
 }
 
+/* Accumulating form y = alpha (A x) + beta y (the paper's task signature reads and writes the */
+/* result vector, Sec. 3.2): t = the CSR-order row sum with fused multiply-add from +0.0, then */
+/* y_i = fma(alpha, t, beta * y_i), or alpha * t when beta == 0 (y_i is then not read).        */
+void oracle_csr_spmv_axpby(int32_t n_rows, const int32_t *row_ptr, const int32_t *col_idx,
+                           const double *val, double alpha, const double *x, double beta,
+                           double *y)
+{
+    for (int32_t i = 0; i < n_rows; ++i) {
+        double t = 0.0;
+        for (int32_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) t = fma(val[k], x[col_idx[k]], t);
+        y[i] = (beta != 0.0) ? fma(alpha, t, beta * y[i]) : alpha * t;
+    }
+}
+
 /* Same definition with FP32 values, vector and accumulator. */
 void oracle_csr_spmv_f32(int32_t n_rows, const int32_t *row_ptr, const int32_t *col_idx,
                          const float *val, const float *x, float *y, int use_fma)

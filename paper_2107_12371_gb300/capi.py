@@ -47,7 +47,8 @@ class spmv_info_t(ctypes.Structure):
                 ("reorder", ctypes.c_int32), ("n_slices", ctypes.c_int32),
                 ("sell_entries", ctypes.c_int64), ("bandwidth", ctypes.c_int32),
                 ("max_slice_span", ctypes.c_int32), ("window_words", ctypes.c_int32),
-                ("device_bytes", ctypes.c_size_t), ("index_bits", ctypes.c_int32)]
+                ("device_bytes", ctypes.c_size_t), ("index_bits", ctypes.c_int32),
+                ("n_cols", ctypes.c_int32)]
 
 
 class cg_options_t(ctypes.Structure):
@@ -94,6 +95,8 @@ _SIGS = {
     "spmv_export_sell": [_P, _P, _P, _P, _P, _P],
     "spmv_apply": [_P, _P, _P, _P],
     "spmv_apply_f32": [_P, _P, _P, _P],
+    "spmv_apply_axpby": [_P, ctypes.c_double, _P, ctypes.c_double, _P, _P],
+    "spmv_apply_axpby_f32": [_P, ctypes.c_float, _P, ctypes.c_float, _P, _P],
     "spmv_apply_csr": [_P, _P, _P, _P],
     "spmv_apply_multi": [_P, _int, _P, _P, _P],
     "spmv_apply_multi_f32": [_P, _int, _P, _P, _P],
@@ -180,9 +183,11 @@ def cg_default_options(**overrides):
     return o
 
 
-def spmv_create(n, row_ptr, col_idx, values, options=None, stream=None, raw_status=False):
+def spmv_create(n, row_ptr, col_idx, values, options=None, stream=None, raw_status=False,
+                n_cols=None):
     """Create a handle from CSR given as numpy host arrays or torch device tensors
-    (int32 row_ptr/col_idx, float64 values).  Returns the handle (an int)."""
+    (int32 row_ptr/col_idx, float64 values); n rows, n_cols columns (default n).
+    Returns the handle (an int)."""
     L = load()
     on_dev = not isinstance(row_ptr, np.ndarray)
     if not on_dev:
@@ -193,7 +198,8 @@ def spmv_create(n, row_ptr, col_idx, values, options=None, stream=None, raw_stat
     else:
         nnz = int(col_idx.numel())
     h = _P()
-    st = L.spmv_create(int(n), int(n), nnz, _ptr(row_ptr), _ptr(col_idx), _ptr(values),
+    st = L.spmv_create(int(n), int(n if n_cols is None else n_cols), nnz, _ptr(row_ptr),
+                       _ptr(col_idx), _ptr(values),
                        int(on_dev), ctypes.byref(options) if options is not None else None,
                        _stream(stream), ctypes.byref(h))
     if raw_status:
@@ -241,6 +247,16 @@ def spmv_export_sell(h, with_values=True):
 
 def spmv_apply(h, x, y, stream=None):
     _check(load().spmv_apply(h, _ptr(x), _ptr(y), _stream(stream)), "spmv_apply")
+
+
+def spmv_apply_axpby(h, alpha, x, beta, y, stream=None):
+    _check(load().spmv_apply_axpby(h, float(alpha), _ptr(x), float(beta), _ptr(y),
+                                   _stream(stream)), "spmv_apply_axpby")
+
+
+def spmv_apply_axpby_f32(h, alpha, x, beta, y, stream=None):
+    _check(load().spmv_apply_axpby_f32(h, float(alpha), _ptr(x), float(beta), _ptr(y),
+                                       _stream(stream)), "spmv_apply_axpby_f32")
 
 
 def spmv_apply_f32(h, x, y, stream=None):
@@ -338,11 +354,13 @@ def spmv_server_destroy(s):
 class Matrix:
     """Owning wrapper of a matrix handle (destroyed with the object)."""
 
-    def __init__(self, n, row_ptr, col_idx, values, stream=None, **options):
+    def __init__(self, n, row_ptr, col_idx, values, stream=None, n_cols=None, **options):
         self.n = int(n)
+        self.n_cols = int(n if n_cols is None else n_cols)
         self.nnz = int(col_idx.size if isinstance(col_idx, np.ndarray) else col_idx.numel())
         self.options = spmv_default_options(**options)
-        self.handle = spmv_create(self.n, row_ptr, col_idx, values, self.options, stream)
+        self.handle = spmv_create(self.n, row_ptr, col_idx, values, self.options, stream,
+                                  n_cols=self.n_cols)
 
     def info(self):
         return spmv_get_info(self.handle)
@@ -352,6 +370,12 @@ class Matrix:
 
     def apply_f32(self, x, y, stream=None):
         spmv_apply_f32(self.handle, x, y, stream)
+
+    def apply_axpby(self, alpha, x, beta, y, stream=None):
+        if x.dtype.itemsize == 4:
+            spmv_apply_axpby_f32(self.handle, alpha, x, beta, y, stream)
+        else:
+            spmv_apply_axpby(self.handle, alpha, x, beta, y, stream)
 
     def apply_csr(self, x, y, stream=None):
         spmv_apply_csr(self.handle, x, y, stream)

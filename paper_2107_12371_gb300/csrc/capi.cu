@@ -102,11 +102,14 @@ spmv_status_t spmv_create(int32_t n_rows, int32_t n_cols, int64_t nnz, const int
                           const spmv_options_t *opt, void *stream, spmv_matrix_t *out) {
     if (!out) return SPMV_ERR_INVALID_ARG;
     *out = nullptr;
-    if (n_rows < 0 || n_cols != n_rows || nnz < 0 || nnz > INT32_MAX) return SPMV_ERR_INVALID_ARG;
+    if (n_rows < 0 || n_cols < 0 || nnz < 0 || nnz > INT32_MAX) return SPMV_ERR_INVALID_ARG;
     if (!row_ptr) return SPMV_ERR_INVALID_ARG;
     if (nnz > 0 && (!col_idx || !values)) return SPMV_ERR_INVALID_ARG;
     spmv_options_t o;
     GB_TRY(normalize_options(opt, &o));
+    // a symmetric renumbering needs a square matrix
+    if (n_cols != n_rows && (o.reorder != SPMV_REORDER_NONE || o.sigma != 0))
+        return SPMV_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
 
     spmv_matrix_t A = new (std::nothrow) spmv_matrix_s();
@@ -114,6 +117,7 @@ spmv_status_t spmv_create(int32_t n_rows, int32_t n_cols, int64_t nnz, const int
     AllocStream alloc_scope(st);
     A->stream = st;
     A->n = n_rows;
+    A->n_cols = n_cols;
     A->nnz = nnz;
     A->opt = o;
     A->S = o.slice_height;
@@ -176,6 +180,7 @@ spmv_status_t spmv_destroy(spmv_matrix_t A) {
 spmv_status_t spmv_get_info(spmv_matrix_t A, spmv_info_t *info) {
     if (!A || !info) return SPMV_ERR_INVALID_ARG;
     info->n_rows = A->n;
+    info->n_cols = A->n_cols;
     info->nnz = A->nnz;
     info->slice_height = A->S;
     info->block = A->block;
@@ -255,6 +260,26 @@ spmv_status_t spmv_apply_f32(spmv_matrix_t A, const float *x, float *y, void *st
         return SPMV_ERR_INVALID_ARG;
     if (!A->has32()) return SPMV_ERR_UNSUPPORTED;
     return launch_spmv32(A, x, y, (cudaStream_t)stream);
+}
+
+spmv_status_t spmv_apply_axpby(spmv_matrix_t A, double alpha, const double *x, double beta,
+                               double *y, void *stream) {
+    if (!A) return SPMV_ERR_INVALID_ARG;
+    if ((A->n > 0 || A->n_cols > 0) &&
+        (!x || !y || !aligned16(x) || !aligned16(y) || x == y))
+        return SPMV_ERR_INVALID_ARG;
+    if (!A->has64()) return SPMV_ERR_UNSUPPORTED;
+    return launch_axpby64(A, alpha, x, beta, y, (cudaStream_t)stream);
+}
+
+spmv_status_t spmv_apply_axpby_f32(spmv_matrix_t A, float alpha, const float *x, float beta,
+                                   float *y, void *stream) {
+    if (!A) return SPMV_ERR_INVALID_ARG;
+    if ((A->n > 0 || A->n_cols > 0) &&
+        (!x || !y || !aligned16(x) || !aligned16(y) || x == y))
+        return SPMV_ERR_INVALID_ARG;
+    if (!A->has32()) return SPMV_ERR_UNSUPPORTED;
+    return launch_axpby32(A, alpha, x, beta, y, (cudaStream_t)stream);
 }
 
 spmv_status_t spmv_apply_csr(spmv_matrix_t A, const double *x, double *y, void *stream) {

@@ -552,6 +552,7 @@ spmv_status_t cg_solve(spmv_matrix_t A, const double *b, double *x, const cg_opt
     if (!(o.rtol >= 0.0) || o.max_iter < 1 || o.check_every < 0 || o.max_outer < 0 ||
         !(o.inner_rtol > 0.0 && o.inner_rtol < 1.0) || o.timeout_s < 0)
         return SPMV_ERR_INVALID_ARG;
+    if (A->n != A->n_cols) return SPMV_ERR_INVALID_ARG;  // CG needs a square matrix
     if (!A->has64()) return (res->status = SPMV_ERR_UNSUPPORTED);
     if (o.mixed && !A->has32()) return (res->status = SPMV_ERR_UNSUPPORTED);
     if (A->n == 0) {

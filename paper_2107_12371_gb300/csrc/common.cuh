@@ -112,7 +112,8 @@ struct CgWork {
 
 struct spmv_matrix_s {
     cudaStream_t stream = nullptr;  // creation stream: buffers are allocated / freed on it
-    int32_t n = 0;
+    int32_t n = 0;       // rows
+    int32_t n_cols = 0;  // columns (== n unless the matrix is rectangular)
     int64_t nnz = 0;
     spmv_options_t opt{};
     int S = 64;        // rows per slice
@@ -153,6 +154,10 @@ spmv_status_t build_sell(spmv_matrix_t A, int S, cudaStream_t st);
 
 // kernels (spmv.cu)
 spmv_status_t launch_spmv64(spmv_matrix_t A, const double *x, double *y, cudaStream_t st);
+spmv_status_t launch_axpby64(spmv_matrix_t A, double alpha, const double *x, double beta,
+                             double *y, cudaStream_t st);
+spmv_status_t launch_axpby32(spmv_matrix_t A, float alpha, const float *x, float beta, float *y,
+                             cudaStream_t st);
 spmv_status_t launch_spmv32(spmv_matrix_t A, const float *x, float *y, cudaStream_t st);
 spmv_status_t launch_spmv_csr64(spmv_matrix_t A, const double *x, double *y, cudaStream_t st);
 spmv_status_t launch_spmm64(spmv_matrix_t A, int k, const double *X, double *Y, cudaStream_t st);

@@ -22,8 +22,8 @@ inline unsigned blocks_for(int64_t n, int t = kT) {
 // validation: row_ptr[0] = 0, row_ptr[n] = nnz, monotone, columns in range and strictly
 // increasing inside each row.  Bits of *err: 1 ends, 2 monotone, 4 range, 8 order.
 // ---------------------------------------------------------------------------------------
-__global__ void validate_csr(int32_t n, int64_t nnz, const int32_t *rp, const int32_t *ci,
-                             int *err) {
+__global__ void validate_csr(int32_t n, int32_t n_cols, int64_t nnz, const int32_t *rp,
+                             const int32_t *ci, int *err) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0 && (rp[0] != 0 || (int64_t)rp[n] != nnz)) atomicOr(err, 1);
     if (i >= n) return;
@@ -35,7 +35,7 @@ __global__ void validate_csr(int32_t n, int64_t nnz, const int32_t *rp, const in
     int32_t prev = -1;
     for (int32_t k = a; k < b; ++k) {
         int32_t c = ci[k];
-        if (c < 0 || c >= n) {
+        if (c < 0 || c >= n_cols) {
             atomicOr(err, 4);
             return;
         }
@@ -602,7 +602,7 @@ spmv_status_t build_matrix(spmv_matrix_t A, const int32_t *d_rp, const int32_t *
         int *d_err = nullptr;
         GB_CUDA(cudaMallocAsync((void **)&d_err, sizeof(int), st));
         cudaMemsetAsync(d_err, 0, sizeof(int), st);
-        validate_csr<<<blocks_for(n), kT, 0, st>>>(n, nnz, d_rp, d_ci, d_err);
+        validate_csr<<<blocks_for(n), kT, 0, st>>>(n, A->n_cols, nnz, d_rp, d_ci, d_err);
         spmv_status_t s = cuda_status(cudaGetLastError());
         int err = 0;
         if (s == SPMV_OK)

@@ -17,11 +17,14 @@
 namespace gb {
 namespace {
 
-template <typename T, int R, int L, int U, typename ColT>
+// y = A x, or with AXPBY y = alpha (A x) + beta y evaluated as fma(alpha, t, beta y) (y is not
+// read when beta == 0), t being the row sum in column order.
+template <typename T, int R, int L, int U, typename ColT, bool AXPBY>
 __device__ __forceinline__ void spmv_sell_body(int32_t n, int32_t n_slices,
                                                const int64_t *__restrict__ sp, ColT cols,
                                                const T *__restrict__ val,
-                                               const T *__restrict__ x, T *__restrict__ y) {
+                                               const T *__restrict__ x, T *__restrict__ y,
+                                               T alpha, T beta) {
     // L lanes per slice, R rows per lane: S = L R rows per slice
     constexpr int S = L * R;
     const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -66,24 +69,34 @@ __device__ __forceinline__ void spmv_sell_body(int32_t n, int32_t n_slices,
         for (int i = 0; i < R; ++i)
             if (c[i] >= 0) acc[i] = fma_t(v[i], ld_x(x + c[i]), acc[i]);
     }
-    store_rows<T, R>(y, slice * S + (int64_t)lane * R, n, acc);
+    const int64_t row0 = slice * S + (int64_t)lane * R;
+    if constexpr (AXPBY) {
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            if (row0 + i < n)
+                acc[i] = beta != T(0) ? fma_t(alpha, acc[i], beta * y[row0 + i]) : alpha * acc[i];
+        }
+    }
+    store_rows<T, R>(y, row0, n, acc);
 }
 
-template <typename T, int R, int L, int U, typename ColT>
+template <typename T, int R, int L, int U, typename ColT, bool AXPBY>
 __global__ void __launch_bounds__(1024)
 spmv_sell(int32_t n, int32_t n_slices, const int64_t *__restrict__ sp, ColT cols,
-          const T *__restrict__ val, const T *__restrict__ x, T *__restrict__ y) {
-    spmv_sell_body<T, R, L, U, ColT>(n, n_slices, sp, cols, val, x, y);
+          const T *__restrict__ val, const T *__restrict__ x, T *__restrict__ y, T alpha,
+          T beta) {
+    spmv_sell_body<T, R, L, U, ColT, AXPBY>(n, n_slices, sp, cols, val, x, y, alpha, beta);
 }
 
 // FP64 with one or two rows per lane, capped at 32 registers (2 x 1024 threads per SM): a
 // full SM of warps keeps enough loads in flight to stream HBM, which the 16-bit decode would
 // otherwise cost in occupancy.
-template <typename T, int R, int L, int U, typename ColT>
+template <typename T, int R, int L, int U, typename ColT, bool AXPBY>
 __global__ void __launch_bounds__(1024, 2)
 spmv_sell_occ(int32_t n, int32_t n_slices, const int64_t *__restrict__ sp, ColT cols,
-              const T *__restrict__ val, const T *__restrict__ x, T *__restrict__ y) {
-    spmv_sell_body<T, R, L, U, ColT>(n, n_slices, sp, cols, val, x, y);
+              const T *__restrict__ val, const T *__restrict__ x, T *__restrict__ y, T alpha,
+              T beta) {
+    spmv_sell_body<T, R, L, U, ColT, AXPBY>(n, n_slices, sp, cols, val, x, y, alpha, beta);
 }
 
 // naive CSR baseline (Sec. 4.3): the column index is read first, then x[col] from global
@@ -115,18 +128,19 @@ inline unsigned grid_for(int64_t threads, int block) {
 
 // (R, L) per slice height: FP64 lanes read 8R bytes of values (16 B at S = 64, 32 B at
 // S >= 128); FP32 lanes read 16 B (R = 4) or 32 B (R = 8).
-template <typename T, int R, int L, int U>
-spmv_status_t go_sell(spmv_matrix_t A, const T *val, const T *x, T *y, cudaStream_t st) {
+template <typename T, int R, int L, int U, bool AXPBY>
+spmv_status_t go_sell(spmv_matrix_t A, const T *val, const T *x, T *y, T alpha, T beta,
+                      cudaStream_t st) {
     const int block = A->block;
     const unsigned grid = grid_for((int64_t)A->n_slices * L, block);
     auto go = [&](auto c) {
         using ColT = decltype(c);
         if constexpr (sizeof(T) == 8 && R <= 2)
-            spmv_sell_occ<T, R, L, U, ColT><<<grid, block, 0, st>>>(A->n, A->n_slices,
-                                                                    A->slice_ptr.p, c, val, x, y);
+            spmv_sell_occ<T, R, L, U, ColT, AXPBY><<<grid, block, 0, st>>>(
+                A->n, A->n_slices, A->slice_ptr.p, c, val, x, y, alpha, beta);
         else
-            spmv_sell<T, R, L, U, ColT><<<grid, block, 0, st>>>(A->n, A->n_slices, A->slice_ptr.p,
-                                                                c, val, x, y);
+            spmv_sell<T, R, L, U, ColT, AXPBY><<<grid, block, 0, st>>>(
+                A->n, A->n_slices, A->slice_ptr.p, c, val, x, y, alpha, beta);
     };
     if (A->index_bits == 16) go(Cols16{A->sell_col16.p, A->col_start.p});
     else go(Cols32{A->sell_col.p});
@@ -134,22 +148,23 @@ spmv_status_t go_sell(spmv_matrix_t A, const T *val, const T *x, T *y, cudaStrea
     return SPMV_OK;
 }
 
-template <typename T>
-spmv_status_t launch_sell(spmv_matrix_t A, const T *val, const T *x, T *y, cudaStream_t st) {
+template <typename T, bool AXPBY = false>
+spmv_status_t launch_sell(spmv_matrix_t A, const T *val, const T *x, T *y, T alpha = T(1),
+                          T beta = T(0), cudaStream_t st = nullptr) {
     if (A->n == 0) return SPMV_OK;
     if constexpr (sizeof(T) == 8) {
         switch (A->S) {
-            case 32: return go_sell<T, 1, 32, 4>(A, val, x, y, st);
-            case 64: return go_sell<T, 2, 32, 4>(A, val, x, y, st);
-            case 128: return go_sell<T, 4, 32, 2>(A, val, x, y, st);
-            case 256: return go_sell<T, 8, 32, 1>(A, val, x, y, st);
+            case 32: return go_sell<T, 1, 32, 4, AXPBY>(A, val, x, y, alpha, beta, st);
+            case 64: return go_sell<T, 2, 32, 4, AXPBY>(A, val, x, y, alpha, beta, st);
+            case 128: return go_sell<T, 4, 32, 2, AXPBY>(A, val, x, y, alpha, beta, st);
+            case 256: return go_sell<T, 8, 32, 1, AXPBY>(A, val, x, y, alpha, beta, st);
         }
     } else {
         switch (A->S) {
-            case 32: return go_sell<T, 4, 8, 4>(A, val, x, y, st);
-            case 64: return go_sell<T, 4, 16, 4>(A, val, x, y, st);
-            case 128: return go_sell<T, 4, 32, 4>(A, val, x, y, st);
-            case 256: return go_sell<T, 8, 32, 2>(A, val, x, y, st);
+            case 32: return go_sell<T, 4, 8, 4, AXPBY>(A, val, x, y, alpha, beta, st);
+            case 64: return go_sell<T, 4, 16, 4, AXPBY>(A, val, x, y, alpha, beta, st);
+            case 128: return go_sell<T, 4, 32, 4, AXPBY>(A, val, x, y, alpha, beta, st);
+            case 256: return go_sell<T, 8, 32, 2, AXPBY>(A, val, x, y, alpha, beta, st);
         }
     }
     return SPMV_ERR_INVALID_ARG;
@@ -160,12 +175,22 @@ spmv_status_t launch_sell(spmv_matrix_t A, const T *val, const T *x, T *y, cudaS
 spmv_status_t launch_spmv64(spmv_matrix_t A, const double *x, double *y, cudaStream_t st) {
     if (A->variant == SPMV_VARIANT_CSR) return launch_spmv_csr64(A, x, y, st);
     if (A->variant == SPMV_VARIANT_SELL_WINDOW) return launch_window64(A, x, y, st);
-    return launch_sell<double>(A, A->sell_val.p, x, y, st);
+    return launch_sell<double>(A, A->sell_val.p, x, y, 1.0, 0.0, st);
+}
+
+spmv_status_t launch_axpby64(spmv_matrix_t A, double alpha, const double *x, double beta,
+                             double *y, cudaStream_t st) {
+    return launch_sell<double, true>(A, A->sell_val.p, x, y, alpha, beta, st);
+}
+
+spmv_status_t launch_axpby32(spmv_matrix_t A, float alpha, const float *x, float beta, float *y,
+                             cudaStream_t st) {
+    return launch_sell<float, true>(A, A->sell_val32.p, x, y, alpha, beta, st);
 }
 
 spmv_status_t launch_spmv32(spmv_matrix_t A, const float *x, float *y, cudaStream_t st) {
     if (A->variant == SPMV_VARIANT_SELL_WINDOW) return launch_window32(A, x, y, st);
-    return launch_sell<float>(A, A->sell_val32.p, x, y, st);
+    return launch_sell<float>(A, A->sell_val32.p, x, y, 1.0f, 0.0f, st);
 }
 
 spmv_status_t launch_spmv_csr64(spmv_matrix_t A, const double *x, double *y, cudaStream_t st) {

@@ -46,7 +46,8 @@ ELEM_HEX, ELEM_PRISM, ELEM_TET = 0, 1, 2
 
 @dataclass
 class CsrMatrix:
-    """A square CSR matrix with strictly increasing columns in every row."""
+    """A CSR matrix (n rows, n_cols columns, square unless n_cols is given) with strictly
+    increasing columns in every row."""
 
     n: int
     row_ptr: np.ndarray  # int32[n + 1]
@@ -54,13 +55,18 @@ class CsrMatrix:
     values: np.ndarray  # float64[nnz]
     perm: np.ndarray | None = None  # new -> old cell index of the random permutation
     info: dict = field(default_factory=dict)
+    n_cols: int | None = None
+
+    def __post_init__(self):
+        if self.n_cols is None:
+            self.n_cols = self.n
 
     @property
     def nnz(self) -> int:
         return int(self.row_ptr[-1])
 
     def to_dense(self) -> np.ndarray:
-        a = np.zeros((self.n, self.n))
+        a = np.zeros((self.n, self.n_cols))
         rows = np.repeat(np.arange(self.n), np.diff(self.row_ptr))
         a[rows, self.col_idx] = self.values
         return a
@@ -360,6 +366,8 @@ def _build(nx, ny, nz, choice, jitter, rng, dirichlet, permute, periodic):
     info = dict(
         nx=nx, ny=ny, nz=nz, h=h, jitter=jitter, dirichlet=dirichlet,
         periodic=periodic, n_boundary_faces=n_bfaces,
+        # interior faces in the final numbering: lower cell, higher cell, area, distance
+        faces=(np.minimum(inv[pi], inv[pj]), np.maximum(inv[pi], inv[pj]), pair_area, dist),
     )
     return CsrMatrix(
         n=n_cells,
@@ -405,6 +413,39 @@ def mixed_matrix(n, ny=None, nz=None, *, p_hex=1 / 3, p_prism=1 / 3, jitter=0.2,
     m.info["kind"] = "mixed"
     m.info["seed"] = seed
     return m, rng
+
+
+def kuhn_tet_operators(n, ny=None, nz=None, *, jitter=0.2, seed=0, permute=True):
+    """Operators of the operator-based finite-volume formulation (Sec. 2) on the Kuhn-tet mesh
+    of :func:`kuhn_tet_matrix`: with interior faces f = (lo, hi) numbered by (lo, hi),
+
+    * G (faces x cells): (G x)_f = (x_hi - x_lo) / d_f, the face-normal gradient;
+    * M (cells x faces): (M u)_i = sum over faces of i of +area_f u_f (i = lo) or -area_f u_f
+      (i = hi), the divergence of face fluxes;
+
+    so that M G equals the Neumann Laplacian L (off-diagonal area/d, diagonal minus their sum)
+    up to rounding.  Returns (M, G, L, rng) with L built from the same draws."""
+    L, rng = kuhn_tet_matrix(n, ny, nz, jitter=jitter, seed=seed, dirichlet=False,
+                             permute=permute)
+    lo, hi, area, dist = L.info["faces"]
+    order = np.lexsort((hi, lo))
+    lo, hi, area, dist = lo[order], hi[order], area[order], dist[order]
+    F = lo.size
+    N = L.n
+    g_rp = (np.arange(F + 1) * 2).astype(np.int32)
+    g_ci = np.stack([lo, hi], axis=1).ravel().astype(np.int32)
+    inv_d = 1.0 / dist
+    g_v = np.stack([-inv_d, inv_d], axis=1).ravel()
+    G = CsrMatrix(F, g_rp, g_ci, g_v, n_cols=N)
+    rows = np.concatenate([lo, hi])
+    cols = np.concatenate([np.arange(F), np.arange(F)])
+    vals = np.concatenate([area, -area])
+    o = np.lexsort((cols, rows))
+    rows, cols, vals = rows[o], cols[o], vals[o]
+    m_rp = np.zeros(N + 1, dtype=np.int64)
+    np.cumsum(np.bincount(rows, minlength=N), out=m_rp[1:])
+    M = CsrMatrix(N, m_rp.astype(np.int32), cols.astype(np.int32), vals, n_cols=F)
+    return M, G, L, rng
 
 
 def uniform_vectors(rng, n, k=None, dtype=np.float64):

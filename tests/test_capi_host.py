@@ -66,8 +66,10 @@ def test_create_rejects_bad_arguments_before_device_work(lib):
     L = lib
     # out == NULL
     assert L.spmv_create(1, 1, 0, None, None, None, 0, None, None, None) == capi.SPMV_ERR_INVALID_ARG
-    # non-square
-    assert L.spmv_create(2, 3, 0, None, None, None, 0, None, None, ctypes.byref(h)) == \
+    # a rectangular matrix cannot be renumbered symmetrically
+    o = capi.spmv_default_options(reorder=capi.SPMV_REORDER_RCM)
+    rp3 = (ctypes.c_int32 * 3)(0, 0, 0)
+    assert L.spmv_create(2, 3, 0, rp3, None, None, 0, ctypes.byref(o), None, ctypes.byref(h)) == \
         capi.SPMV_ERR_INVALID_ARG
     assert h.value is None
     # negative sizes, missing arrays
@@ -90,6 +92,7 @@ def test_entry_points_reject_null_handles(lib):
     L = lib
     assert L.spmv_apply(None, None, None, None) == capi.SPMV_ERR_INVALID_ARG
     assert L.spmv_apply_f32(None, None, None, None) == capi.SPMV_ERR_INVALID_ARG
+    assert L.spmv_apply_axpby(None, 1.0, None, 0.0, None, None) == capi.SPMV_ERR_INVALID_ARG
     assert L.spmv_apply_multi(None, 8, None, None, None) == capi.SPMV_ERR_INVALID_ARG
     assert L.spmv_permute(None, 0, 8, None, None, None) == capi.SPMV_ERR_INVALID_ARG
     assert L.spmv_get_info(None, None) == capi.SPMV_ERR_INVALID_ARG

@@ -145,6 +145,59 @@ def test_window_variant_wide_and_ragged(oracle):
     check_fp64(m, x, gpu_spmv(A, x), oracle)
 
 
+@pytest.mark.parametrize("alpha,beta", [(1.0, 0.0), (2.5, -0.75), (-1.0, 1.0)])
+@pytest.mark.parametrize("S", [32, 64, 128])
+def test_axpby_parity(oracle, S, alpha, beta):
+    """y = alpha A x + beta y (Sec. 3.2's read-write result vector), bit-identical to the oracle;
+    with beta == 0 a NaN-filled y is never read."""
+    m, x = workloads.c1()
+    y0 = np.random.default_rng(7).uniform(-1, 1, m.n)
+    A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values, slice_height=S,
+                    precision=capi.SPMV_PREC_DUAL)
+    yd = dev(y0 if beta != 0 else np.full(m.n, np.nan))
+    A.apply_axpby(alpha, dev(x), beta, yd)
+    torch.cuda.synchronize()
+    ref = oracle.spmv_axpby(m.row_ptr, m.col_idx, m.values, alpha, x, beta, y0)
+    assert np.array_equal(yd.cpu().numpy(), ref)
+    # FP32 form: finite and within FP32 rounding of the FP64 result
+    y32 = dev(y0.astype(np.float32))
+    A.apply_axpby(alpha, dev(x.astype(np.float32)), beta, y32)
+    torch.cuda.synchronize()
+    mag = abs(alpha) * absrow(m, x) + abs(beta) * np.abs(y0)
+    assert np.all(np.abs(y32.cpu().numpy() - ref) <= 32 * 2.0 ** -24 * mag + 1e-30)
+
+
+def test_rectangular_operators_parity(oracle):
+    """Rectangular divergence M (cells x faces) and gradient G (faces x cells) of the
+    operator-based formulation (Sec. 2): each product bit-identical to the oracle, and the chain
+    M (G x) equal to the Laplacian's product within rounding."""
+    M, G, L, rng = meshgen.kuhn_tet_operators(12, seed=4)
+    x = meshgen.uniform_vectors(rng, L.n)
+    Gh = capi.Matrix(G.n, G.row_ptr, G.col_idx, G.values, n_cols=G.n_cols)
+    Mh = capi.Matrix(M.n, M.row_ptr, M.col_idx, M.values, n_cols=M.n_cols)
+    assert Gh.info()["n_cols"] == L.n and Mh.info()["n_cols"] == G.n
+    xd = dev(x)
+    gx = torch.empty(G.n, dtype=torch.float64, device="cuda")
+    y = torch.empty(M.n, dtype=torch.float64, device="cuda")
+    Gh.apply(xd, gx)
+    Mh.apply(gx, y)
+    torch.cuda.synchronize()
+    ref_g = oracle.spmv(G.row_ptr, G.col_idx, G.values, x, use_fma=True)
+    assert np.array_equal(gx.cpu().numpy(), ref_g)
+    ref_y = oracle.spmv(M.row_ptr, M.col_idx, M.values, ref_g, use_fma=True)
+    assert np.array_equal(y.cpu().numpy(), ref_y)
+    lx = oracle.spmv(L.row_ptr, L.col_idx, L.values, x)
+    scale = np.add.reduceat(np.abs(L.values), L.row_ptr[:-1]) * np.abs(x).max()
+    assert np.all(np.abs(y.cpu().numpy() - lx) <= 1e-13 * scale)
+    # rectangular matrices cannot be renumbered symmetrically, nor solved by CG
+    st, h = capi.spmv_create(G.n, G.row_ptr, G.col_idx, G.values, raw_status=True, n_cols=L.n,
+                             options=capi.spmv_default_options(reorder=capi.SPMV_REORDER_RCM))
+    assert st == capi.SPMV_ERR_INVALID_ARG
+    res = Gh.solve(dev(np.ones(G.n)), torch.zeros(G.n, dtype=torch.float64, device="cuda"),
+                   raise_on_error=False)
+    assert res["status"] == capi.SPMV_ERR_INVALID_ARG
+
+
 def test_c1_naive_csr_parity(oracle):
     m, x = workloads.c1()
     A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values)

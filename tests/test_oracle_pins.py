@@ -264,6 +264,36 @@ def test_spmv_bloch_modes_periodic_kuhn(oracle):
                 assert np.abs(y - lam[e] * part).max() <= 1e-13 * 20 * h
 
 
+def test_operators_divergence_of_gradient_is_laplacian(oracle):
+    """Sec. 2 operator form: M (G x) equals the Neumann Laplacian L x (same faces, same draws)
+    up to rounding, checked with the oracle's rectangular CSR products."""
+    M, G, L, rng = meshgen.kuhn_tet_operators(6, seed=2)
+    x = meshgen.uniform_vectors(rng, L.n)
+    assert (M.n, M.n_cols, G.n, G.n_cols) == (L.n, G.n, M.n_cols, L.n)
+    assert G.n == (L.nnz - L.n) // 2  # one face per pair of off-diagonals
+    gx = oracle.spmv(G.row_ptr, G.col_idx, G.values, x)
+    y = oracle.spmv(M.row_ptr, M.col_idx, M.values, gx)
+    ref = oracle.spmv(L.row_ptr, L.col_idx, L.values, x)
+    scale = np.add.reduceat(np.abs(L.values), L.row_ptr[:-1]) * np.abs(x).max()
+    assert np.all(np.abs(y - ref) <= 1e-13 * scale)
+    D = M.to_dense() @ G.to_dense()
+    np.testing.assert_allclose(D, L.to_dense(), rtol=0, atol=1e-13 * np.abs(L.values).max())
+
+
+def test_spmv_axpby_matches_definition(oracle):
+    m, rng = meshgen.kuhn_tet_matrix(4, seed=3, dirichlet=True)
+    x = meshgen.uniform_vectors(rng, m.n)
+    y0 = meshgen.uniform_vectors(rng, m.n)
+    A = m.to_dense()
+    for alpha, beta in [(1.0, 0.0), (2.5, -0.75), (-1.0, 1.0)]:
+        y = oracle.spmv_axpby(m.row_ptr, m.col_idx, m.values, alpha, x, beta, y0)
+        ref = alpha * (A @ x) + beta * y0
+        mag = abs(alpha) * (np.abs(A) @ np.abs(x)) + abs(beta) * np.abs(y0)
+        assert np.all(np.abs(y - ref) <= 8 * 2.0 ** -53 * mag)
+    y = oracle.spmv_axpby(m.row_ptr, m.col_idx, m.values, 1.0, x, 0.0, np.full(m.n, np.nan))
+    assert np.all(np.isfinite(y))  # beta == 0 never reads y
+
+
 def test_spmv_f32_within_rounding_bound(oracle):
     m, rng = meshgen.kuhn_tet_matrix(5, seed=2, dirichlet=True)
     x = meshgen.uniform_vectors(rng, m.n)
