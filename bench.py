@@ -231,6 +231,36 @@ def time_kernel(torch, fn, steps, flush_buf, stream):
     return [a.elapsed_time(b) for a, b in evs]
 
 
+def run_profile_kernel(args):
+    """A few launches of one secondary kernel, for ncu captures (no timing output)."""
+    import torch
+    from paper_2107_12371_gb300 import capi, meshgen, workloads
+    capi.load()
+    dev = torch.device("cuda", 0)
+    what = args.profile_kernel
+    if what.startswith("spmm"):
+        k, dt = int(what.split("_")[1][1:]), what.split("_")[2]
+        m, X = workloads.mixed(87, seed=1, k=32)
+        A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values, reorder=capi.SPMV_REORDER_RCM,
+                        precision=capi.SPMV_PREC_DUAL, sigma=1024)
+        Xd = torch.from_numpy(np.ascontiguousarray(X[:, :k])).to(
+            dev, torch.float64 if dt == "f64" else torch.float32)
+        Yd = torch.empty_like(Xd)
+        for _ in range(args.steps):
+            A.apply_multi(Xd, Yd)
+    elif what == "chain":
+        M, G, L, rng = meshgen.kuhn_tet_operators(80, seed=0, permute=False)
+        Gh = capi.Matrix(G.n, G.row_ptr, G.col_idx, G.values, n_cols=G.n_cols)
+        Mh = capi.Matrix(M.n, M.row_ptr, M.col_idx, M.values, n_cols=M.n_cols)
+        xd = torch.from_numpy(meshgen.uniform_vectors(rng, L.n)).to(dev)
+        y = torch.empty(M.n, dtype=torch.float64, device=dev)
+        for _ in range(args.steps):
+            capi.spmv_apply_chain(Mh.handle, Gh.handle, xd, y)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_kernel": what}), flush=True)
+    return 0
+
+
 def run_gpu(args):
     import torch
     from paper_2107_12371_gb300 import capi, workloads
@@ -427,6 +457,7 @@ def secondary(args, torch, capi, workloads, m, x, A, xi, stream, flush, dev):
     R.close()
     out.update(cg_results(torch, capi, m, x, A, xi, dev))
     out.update(spmm_results(args, torch, capi, workloads, flush, stream, dev))
+    out.update(chain_results(args, torch, capi, flush, stream, dev))
     return out
 
 
@@ -506,6 +537,38 @@ def spmm_results(args, torch, capi, workloads, flush, stream, dev):
                                 "index_bits": info["index_bits"], "sigma": 1024,
                                 "sell_entries_over_nnz": info["sell_entries"] / m.nnz,
                                 "sell_entries_over_nnz_unsorted": padded_plain / m.nnz, **out}}
+
+
+def chain_results(args, torch, capi, flush, stream, dev):
+    """Operator chain of the operator-based formulation: y = M (G x) with the gradient G
+    (faces x cells) and the divergence M (cells x faces) of the 80^3 Kuhn-tet mesh (3.07M
+    cells, 6.1M faces): two separate products against the fused chain."""
+    from paper_2107_12371_gb300 import meshgen
+    M, G, L, rng = meshgen.kuhn_tet_operators(80, seed=0, permute=False)
+    x = meshgen.uniform_vectors(rng, L.n)
+    Gh = capi.Matrix(G.n, G.row_ptr, G.col_idx, G.values, stream=stream, n_cols=G.n_cols)
+    Mh = capi.Matrix(M.n, M.row_ptr, M.col_idx, M.values, stream=stream, n_cols=M.n_cols)
+    xd = torch.from_numpy(x).to(dev)
+    t = torch.empty(G.n, dtype=torch.float64, device=dev)
+    y = torch.empty(M.n, dtype=torch.float64, device=dev)
+    K = max(10, min(args.steps, 50))
+
+    def sep():
+        Gh.apply(xd, t, stream)
+        Mh.apply(t, y, stream)
+    ts = time_kernel(torch, sep, K, flush, stream)
+    tf = time_kernel(torch, lambda: capi.spmv_apply_chain(Mh.handle, Gh.handle, xd, y, stream),
+                     K, flush, stream)
+    ms_sep, ms_fused = sum(ts) / len(ts), sum(tf) / len(tf)
+    nbytes = 12 * (M.nnz + G.nnz) + 8 * (L.n + 2 * G.n + L.n)
+    Gh.close()
+    Mh.close()
+    return {"operator_chain": {
+        "mesh": "kuhn-tet 80^3, %d cells, %d faces" % (L.n, G.n),
+        "separate_ms": ms_sep, "fused_ms": ms_fused, "speedup": ms_sep / ms_fused,
+        "algorithmic_bytes_two_products": nbytes,
+        "separate_GBs": nbytes / (ms_sep / 1e3) / 1e9,
+        "fused_GBs_same_bytes": nbytes / (ms_fused / 1e3) / 1e9}}
 
 
 def _make_request(args):
@@ -604,6 +667,8 @@ def main():
     ap.add_argument("--index-bits", type=int, default=0, choices=[0, 16, 32])
     ap.add_argument("--f32", action="store_true",
                     help="with --profile: time the FP32 product of the handle instead")
+    ap.add_argument("--profile-kernel", default="",
+                    help="spmm_k8_f64 | spmm_k32_f32 | ... | chain: launch only that kernel")
     ap.add_argument("--profile-cg", type=int, default=0,
                     help="with --profile: also run CG solves capped at this many iterations")
     ap.add_argument("--serve-requests", type=int, default=48)
@@ -615,6 +680,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_kernel:
+        return run_profile_kernel(args)
     return run_gpu(args)
 
 

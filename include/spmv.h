@@ -181,6 +181,18 @@ spmv_status_t spmv_apply_multi(spmv_matrix_t A, int k, const double *X_dev, doub
 spmv_status_t spmv_apply_multi_f32(spmv_matrix_t A, int k, const float *X_dev, float *Y_dev,
                                    void *stream);
 
+/*
+ * spmv_apply_chain -- async.  y = B (C x) for an operator chain (the operator-based formulation
+ * evaluates a time step as chains of sparse products, Sec. 2), without writing C x to memory:
+ * each entry b_if of B evaluates t_f = sum_j c_fj x_j over row f of C in column order with
+ * fused multiply-add from +0.0, and y_i = sum_f b_if t_f in B's column order, so y equals
+ * spmv_apply(B, spmv_apply(C, x)) bit for bit.  Requires B's columns = C's rows
+ * (B->n_cols == C->n_rows) and neither handle renumbered (no reorder, no sigma); FP64 values.
+ * x: device double[C n_cols]; y: device double[B n_rows], 16-byte aligned, not overlapping x.
+ */
+spmv_status_t spmv_apply_chain(spmv_matrix_t B, spmv_matrix_t C, const double *x_dev,
+                               double *y_dev, void *stream);
+
 /* async.  Converts a vector between the caller's numbering and the internal one:
  * direction 0: out[new] = in[perm[new]]; direction 1: out[perm[new]] = in[new].
  * elem_bytes 4 or 8; in/out device arrays of n_rows elements, must not overlap. */

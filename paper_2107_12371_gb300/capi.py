@@ -98,6 +98,7 @@ _SIGS = {
     "spmv_apply_axpby": [_P, ctypes.c_double, _P, ctypes.c_double, _P, _P],
     "spmv_apply_axpby_f32": [_P, ctypes.c_float, _P, ctypes.c_float, _P, _P],
     "spmv_apply_csr": [_P, _P, _P, _P],
+    "spmv_apply_chain": [_P, _P, _P, _P, _P],
     "spmv_apply_multi": [_P, _int, _P, _P, _P],
     "spmv_apply_multi_f32": [_P, _int, _P, _P, _P],
     "spmv_permute": [_P, _int, _int, _P, _P, _P],
@@ -261,6 +262,11 @@ def spmv_apply_axpby_f32(h, alpha, x, beta, y, stream=None):
 
 def spmv_apply_f32(h, x, y, stream=None):
     _check(load().spmv_apply_f32(h, _ptr(x), _ptr(y), _stream(stream)), "spmv_apply_f32")
+
+
+def spmv_apply_chain(hb, hc, x, y, stream=None):
+    """y = B (C x) without materialising C x."""
+    _check(load().spmv_apply_chain(hb, hc, _ptr(x), _ptr(y), _stream(stream)), "spmv_apply_chain")
 
 
 def spmv_apply_csr(h, x, y, stream=None):

@@ -189,6 +189,13 @@ def test_rectangular_operators_parity(oracle):
     lx = oracle.spmv(L.row_ptr, L.col_idx, L.values, x)
     scale = np.add.reduceat(np.abs(L.values), L.row_ptr[:-1]) * np.abs(x).max()
     assert np.all(np.abs(y.cpu().numpy() - lx) <= 1e-13 * scale)
+    # the fused chain: y = M (G x) without writing G x, bit-identical to the two products
+    for S in (32, 64, 128, 256):
+        Ms = capi.Matrix(M.n, M.row_ptr, M.col_idx, M.values, n_cols=M.n_cols, slice_height=S)
+        yc = torch.empty_like(y)
+        capi.spmv_apply_chain(Ms.handle, Gh.handle, xd, yc)
+        torch.cuda.synchronize()
+        assert np.array_equal(yc.cpu().numpy(), ref_y), S
     # rectangular matrices cannot be renumbered symmetrically, nor solved by CG
     st, h = capi.spmv_create(G.n, G.row_ptr, G.col_idx, G.values, raw_status=True, n_cols=L.n,
                              options=capi.spmv_default_options(reorder=capi.SPMV_REORDER_RCM))
