@@ -232,6 +232,16 @@ spmv_status_t cg_default_options(cg_options_t *opt);
 spmv_status_t cg_solve(spmv_matrix_t A, const double *b_dev, double *x_dev, const cg_options_t *opt,
                        cg_result_t *result, void *stream);
 
+/*
+ * spmv_diag_barrier_timeout -- sync.  Self-test of the failure path of the persistent CG
+ * kernel's bounded waits (not in the paper): launches `ctas` co-resident CTAs (1 <= ctas <= SM
+ * count) on the kernel's grid barrier configured to expect one CTA more than exist, so no
+ * wait is ever released; every CTA gives up after limit_s seconds (0 < limit_s <= 10) and
+ * records the timeout.  Returns SPMV_ERR_TIMEOUT when the device reported the timeout as
+ * designed, SPMV_ERR_CUDA otherwise.  Nothing faults or hangs.
+ */
+spmv_status_t spmv_diag_barrier_timeout(int ctas, double limit_s, void *stream);
+
 /* ------------------------------ allocation-free solve ----------------------------------- */
 /* Largest system (rows) that cg_solve_csr_noalloc accepts. */
 #define SPMV_NOALLOC_MAX_ROWS 65536

@@ -104,6 +104,7 @@ _SIGS = {
     "spmv_permute": [_P, _int, _int, _P, _P, _P],
     "cg_default_options": [ctypes.POINTER(cg_options_t)],
     "cg_solve": [_P, _P, _P, ctypes.POINTER(cg_options_t), ctypes.POINTER(cg_result_t), _P],
+    "spmv_diag_barrier_timeout": [_int, ctypes.c_double, _P],
     "cg_solve_csr_noalloc": [_i32, _i64, _P, _P, _P, _P, _P, ctypes.POINTER(cg_options_t),
                              ctypes.POINTER(cg_result_t), _P],
     "spmv_server_create": [ctypes.c_size_t, _int, ctypes.POINTER(_P)],

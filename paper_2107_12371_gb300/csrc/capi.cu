@@ -58,6 +58,7 @@ static spmv_status_t normalize_options(const spmv_options_t *in, spmv_options_t 
 
 void release_matrix(spmv_matrix_t A);
 spmv_status_t autotune_matrix(spmv_matrix_t A, cudaStream_t st);
+spmv_status_t diag_barrier_timeout(int ctas, double limit_s, int *done_out, cudaStream_t st);
 
 }  // namespace gb
 
@@ -304,6 +305,14 @@ spmv_status_t spmv_apply_multi_f32(spmv_matrix_t A, int k, const float *X, float
         return SPMV_ERR_INVALID_ARG;
     if (!A->has32()) return SPMV_ERR_UNSUPPORTED;
     return launch_spmm32(A, k, X, Y, (cudaStream_t)stream);
+}
+
+spmv_status_t spmv_diag_barrier_timeout(int ctas, double limit_s, void *stream) {
+    if (ctas < 1 || ctas > device_facts().sm_count || !(limit_s > 0.0) || limit_s > 10.0)
+        return SPMV_ERR_INVALID_ARG;
+    int done = 0;
+    GB_TRY(diag_barrier_timeout(ctas, limit_s, &done, (cudaStream_t)stream));
+    return done == 4 ? SPMV_ERR_TIMEOUT : SPMV_ERR_CUDA;
 }
 
 spmv_status_t spmv_permute(spmv_matrix_t A, int direction, int elem_bytes, const void *in,

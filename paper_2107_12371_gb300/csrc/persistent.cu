@@ -22,8 +22,12 @@ __device__ __forceinline__ long long global_timer_ns() {
 
 constexpr long long kBarrierLimitNs = 2000000000LL;
 
-__device__ bool grid_barrier(CgScalars *sc) {
+// Grid barrier over `expected` CTAs (gridDim.x in the solver).  A CTA that waits longer than
+// limit_ns records done = 4 and returns false instead of spinning on.
+__device__ bool grid_barrier(CgScalars *sc, unsigned expected = 0,
+                             long long limit_ns = kBarrierLimitNs) {
     __shared__ int ok;
+    if (expected == 0) expected = gridDim.x;
     __syncthreads();
     if (threadIdx.x == 0) {
         volatile unsigned *genp = &sc->bar_gen;
@@ -31,14 +35,14 @@ __device__ bool grid_barrier(CgScalars *sc) {
         __threadfence();
         const unsigned arrived = atomicAdd(&sc->bar_count, 1u);
         int good = 1;
-        if (arrived == gridDim.x - 1) {
+        if (arrived == expected - 1) {
             atomicExch(&sc->bar_count, 0u);
             __threadfence();
             atomicAdd(&sc->bar_gen, 1u);
         } else {
             const long long t0 = global_timer_ns();
             while (*genp == g) {
-                if (global_timer_ns() - t0 > kBarrierLimitNs) {
+                if (global_timer_ns() - t0 > limit_ns) {
                     good = 0;
                     atomicExch(&sc->done, 4);
                     break;
@@ -164,7 +168,32 @@ cg_persistent(int32_t n, int32_t n_slices, const int64_t *sp, ColT col,
     }
 }
 
+// Diagnostic: a barrier that expects one CTA more than the grid has, so no wait can ever be
+// released -- every CTA must leave through the time limit and record done = 4.
+__global__ void barrier_timeout_probe(CgScalars *sc, long long limit_ns) {
+    grid_barrier(sc, gridDim.x + 1, limit_ns);
+}
+
 }  // namespace
+
+spmv_status_t diag_barrier_timeout(int ctas, double limit_s, int *done_out, cudaStream_t st) {
+    CgScalars *sc = nullptr;
+    GB_CUDA(cudaMallocAsync((void **)&sc, sizeof(CgScalars), st));
+    spmv_status_t s = cuda_status(cudaMemsetAsync(sc, 0, sizeof(CgScalars), st));
+    long long limit_ns = (long long)(limit_s * 1e9);
+    void *args[] = {&sc, &limit_ns};
+    if (s == SPMV_OK)
+        s = cuda_status(cudaLaunchCooperativeKernel((const void *)barrier_timeout_probe,
+                                                    dim3(ctas), dim3(32), args, 0, st));
+    CgScalars h{};
+    if (s == SPMV_OK)
+        s = cuda_status(cudaMemcpyAsync(&h, sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
+    if (s == SPMV_OK) s = cuda_status(cudaStreamSynchronize(st));
+    cudaFreeAsync(sc, st);
+    cudaStreamSynchronize(st);
+    *done_out = h.done;
+    return s;
+}
 
 spmv_status_t cg_persistent64(spmv_matrix_t A, const cg_options_t &o, CgScalars *out,
                               cudaStream_t st) {

@@ -147,3 +147,18 @@ def test_c2_full_size_solve(oracle, mixed):
     x = torch.empty_like(xi)
     A.permute(1, xi, x)
     assert true_relres(oracle, m, x.cpu().numpy(), b) <= 1e-10
+
+
+def test_barrier_wait_runs_out_with_a_status():
+    """Failure detection without a GPU fault: a grid barrier waiting for a CTA that does not
+    exist gives up after its time limit and reports a timeout; the context stays usable."""
+    import time
+    t0 = time.time()
+    st = capi.load().spmv_diag_barrier_timeout(8, 0.2, None)
+    assert st == capi.SPMV_ERR_TIMEOUT
+    assert time.time() - t0 < 5.0
+    # the device still works afterwards
+    m, b = workloads.kuhn(4, seed=1, dirichlet=True)
+    A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values)
+    _, res = solve(A, b, rtol=1e-10)
+    assert res["status"] == capi.SPMV_OK
