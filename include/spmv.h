@@ -210,6 +210,8 @@ typedef struct {
     int persistent;       /* 1: one cooperative kernel per solve; 0: CUDA-graph batches of iterations */
     int check_every;      /* graph path: iterations per graph launch between host checks (16) */
     double timeout_s;     /* wall-clock limit of the solve, 0 = none                           */
+    int adaptive_inner;   /* mixed: 1 = each inner solve stops at max(inner_rtol,
+                           * 0.5 rtol ||b|| / ||r||), the reduction still missing (default 1) */
 } cg_options_t;
 
 typedef struct {

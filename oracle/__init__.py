@@ -78,7 +78,7 @@ def lib():
                                         _i32, _PI32, _PF64, _PF64]
         L.oracle_jacobi_pcg.restype = _int
         L.oracle_mixed_ir.argtypes = [_i32, _i32p, _i32p, _f64p, _f64p, _f64p, _f64, _f64, _i32,
-                                      _i32, _PI32, _PI32, _PF64]
+                                      _i32, _int, _PI32, _PI32, _PF64]
         L.oracle_mixed_ir.restype = _int
     return _lib
 
@@ -216,7 +216,7 @@ def jacobi_pcg(row_ptr, col_idx, values, b, x0=None, rtol=1e-10, max_iter=100000
 
 
 def mixed_ir(row_ptr, col_idx, values, b, rtol=1e-10, inner_rtol=1e-4, inner_max_iter=1000,
-             max_outer=20):
+             max_outer=20, adaptive=True):
     """FP32 inner Jacobi-PCG with FP64 iterative refinement.  Returns (x, info dict)."""
     rp, ci = _csr(row_ptr, col_idx)
     n = rp.size - 1
@@ -226,7 +226,7 @@ def mixed_ir(row_ptr, col_idx, values, b, rtol=1e-10, inner_rtol=1e-4, inner_max
     rr = ctypes.c_double(0.0)
     rc = lib().oracle_mixed_ir(n, rp, ci, np.ascontiguousarray(values, np.float64),
                                np.ascontiguousarray(b, np.float64), x, rtol, inner_rtol,
-                               inner_max_iter, max_outer, ctypes.byref(outer),
+                               inner_max_iter, max_outer, int(adaptive), ctypes.byref(outer),
                                ctypes.byref(inner), ctypes.byref(rr))
     if rc < 0:
         raise RuntimeError("oracle_mixed_ir failed: %d" % rc)

@@ -498,6 +498,8 @@ done:
 /*   x = 0; r = b - A x (FP64)                                                              */
 /*   repeat while ||r|| > rtol ||b|| and outer < max_outer:                                 */
 /*     s = ||r||; solve A32 d = fp32(r / s) by FP32 Jacobi-PCG from d = 0 to inner_rtol     */
+/*     (adaptive != 0: to max(inner_rtol, min(0.5, 0.5 rtol ||b|| / ||r||)), the reduction    */
+/*     the outer residual still needs with a factor 2 of margin)                            */
 /*     (FP32 values = fp32(a_ij), FP32 vectors, FP32 SpMV accumulation, dinv32 = 1/a32_ii); */
 /*     x += s * d (FP64); r = b - A x (FP64 values).                                        */
 /* Inner dot products are evaluated exactly enough to be the plain definition: the FP32     */
@@ -541,7 +543,7 @@ static int32_t pcg32(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, 
 
 int oracle_mixed_ir(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, const double *val,
                     const double *b, double *x, double rtol, double inner_rtol,
-                    int32_t inner_max_iter, int32_t max_outer, int32_t *outer_out,
+                    int32_t inner_max_iter, int32_t max_outer, int adaptive, int32_t *outer_out,
                     int32_t *inner_total_out, double *relres_out)
 {
     int64_t nnz = row_ptr[n];
@@ -581,7 +583,12 @@ int oracle_mixed_ir(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, c
         if (outer >= max_outer) { rc = 1; goto done; }
         double s = rnorm;
         for (int32_t i = 0; i < n; ++i) rhs[i] = (float)(r[i] / s);
-        inner_total += pcg32(n, row_ptr, col_idx, val32, dinv, rhs, d, (float)inner_rtol,
+        double tol_in = inner_rtol;
+        if (adaptive) {
+            double need = 0.5 * rtol * bnorm / rnorm;
+            if (need > tol_in) tol_in = need < 0.5 ? need : 0.5;
+        }
+        inner_total += pcg32(n, row_ptr, col_idx, val32, dinv, rhs, d, (float)tol_in,
                              inner_max_iter, rr, z, p, q);
         for (int32_t i = 0; i < n; ++i) x[i] = x[i] + s * (double)d[i];
         ++outer;

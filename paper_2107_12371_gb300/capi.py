@@ -55,7 +55,8 @@ class cg_options_t(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("max_iter", ctypes.c_int), ("mixed", ctypes.c_int),
                 ("inner_rtol", ctypes.c_double), ("max_outer", ctypes.c_int),
                 ("use_x0", ctypes.c_int), ("persistent", ctypes.c_int),
-                ("check_every", ctypes.c_int), ("timeout_s", ctypes.c_double)]
+                ("check_every", ctypes.c_int), ("timeout_s", ctypes.c_double),
+                ("adaptive_inner", ctypes.c_int)]
 
 
 class cg_result_t(ctypes.Structure):

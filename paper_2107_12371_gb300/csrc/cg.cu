@@ -463,7 +463,14 @@ static spmv_status_t solve_mixed(spmv_matrix_t A, const double *b, const cg_opti
             res->status = SPMV_ERR_TIMEOUT;
             break;
         }
-        set_scalars<<<1, 1, 0, st>>>(si, o.inner_rtol * o.inner_rtol, o.max_iter);
+        // inner tolerance: inner_rtol, or (adaptive) just the reduction the outer residual
+        // still needs, with a factor 2 of margin for the FP32 inner solve
+        double tol_in = o.inner_rtol;
+        if (o.adaptive_inner && ho.rr > 0.0) {
+            const double need = 0.5 * o.rtol * std::sqrt(ho.bb / ho.rr);
+            if (need > tol_in) tol_in = need < 0.5 ? need : 0.5;
+        }
+        set_scalars<<<1, 1, 0, st>>>(si, tol_in * tol_in, o.max_iter);
         ir_start_inner<<<G, kCgBlock, 0, st>>>(A->n, w.r.p, so, w.r32.p, w.p32.p, w.d32.p,
                                                w.dinv32.p, w.part.p, si);
         GB_LAUNCHED();
@@ -535,6 +542,7 @@ spmv_status_t cg_default_options(cg_options_t *o) {
     o->persistent = 0;
     o->check_every = 16;
     o->timeout_s = 0.0;
+    o->adaptive_inner = 1;
     return SPMV_OK;
 }
 

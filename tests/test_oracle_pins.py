@@ -506,10 +506,11 @@ def test_pcg_zero_rhs_and_iteration_cap(oracle):
     assert not info["converged"] and info["iterations"] == 3
 
 
-def test_mixed_ir_reaches_fp64_residual(oracle):
+@pytest.mark.parametrize("adaptive", [False, True])
+def test_mixed_ir_reaches_fp64_residual(oracle, adaptive):
     m, rng = meshgen.kuhn_tet_matrix(6, seed=0, dirichlet=True)
     b = meshgen.uniform_vectors(rng, m.n)
-    x, info = oracle.mixed_ir(m.row_ptr, m.col_idx, m.values, b, rtol=1e-10)
+    x, info = oracle.mixed_ir(m.row_ptr, m.col_idx, m.values, b, rtol=1e-10, adaptive=adaptive)
     A = m.to_dense()
     assert info["converged"]
     assert 2 <= info["outer_iterations"] <= 8
