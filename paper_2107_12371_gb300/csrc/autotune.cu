@@ -40,6 +40,7 @@ spmv_status_t time_launch(spmv_matrix_t A, const void *x, void *y, cudaStream_t 
 
 spmv_status_t autotune_matrix(spmv_matrix_t A, cudaStream_t st) {
     if (A->n == 0) return SPMV_OK;
+    NvtxRange nvtx("spmv_create/autotune");
     const size_t eb = A->has64() ? sizeof(double) : sizeof(float);
     void *x = nullptr, *y = nullptr;
     const size_t nx = (size_t)(A->n_cols > 0 ? A->n_cols : 1);

@@ -112,6 +112,7 @@ spmv_status_t spmv_create(int32_t n_rows, int32_t n_cols, int64_t nnz, const int
     if (n_cols != n_rows && (o.reorder != SPMV_REORDER_NONE || o.sigma != 0))
         return SPMV_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
+    NvtxRange nvtx("spmv_create");
 
     spmv_matrix_t A = new (std::nothrow) spmv_matrix_s();
     if (!A) return SPMV_ERR_OOM;

@@ -569,6 +569,7 @@ spmv_status_t cg_solve(spmv_matrix_t A, const double *b, double *x, const cg_opt
     }
     cudaStream_t st = (cudaStream_t)stream;
     AllocStream alloc_scope(st);
+    NvtxRange nvtx(o.mixed ? "cg_solve/mixed" : "cg_solve/fp64");
     const auto t0 = Clock::now();
     spmv_status_t s = ensure_cg_work(A, o.mixed != 0, st);
     if (s != SPMV_OK) return (res->status = s);

@@ -6,9 +6,17 @@
 #include <cstddef>
 #include <cstdint>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/spmv.h"
 
 namespace gb {
+
+// NVTX range for profilers (header-only NVTX v3; no cost when no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
 
 // Number of SMs and other device facts, queried once per device.
 struct DeviceFacts {

@@ -528,6 +528,7 @@ __global__ void relative_cols16(int32_t n_slices, const int64_t *sp, const int32
 }  // namespace
 
 spmv_status_t build_sell(spmv_matrix_t A, int S, cudaStream_t st) {
+    NvtxRange nvtx("spmv_create/sliced_ellpack");
     const int32_t n = A->n;
     const int32_t n_slices = (int32_t)(((int64_t)n + S - 1) / S);
     size_t *tally = &A->bytes;
@@ -618,6 +619,7 @@ spmv_status_t build_matrix(spmv_matrix_t A, const int32_t *d_rp, const int32_t *
     GB_TRY(A->val.alloc((size_t)nnz, tally));
 
     // 2. ordering (Sec. 4.1), optional length sorting inside windows, symmetric permutation
+    NvtxRange nvtx_order("spmv_create/reorder");
     const bool reorder = A->opt.reorder != SPMV_REORDER_NONE;
     const int sigma = A->opt.sigma;
     if ((reorder || sigma > 0) && n > 0) {

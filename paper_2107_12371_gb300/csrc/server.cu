@@ -81,6 +81,7 @@ namespace {
 // duration; they are freed stream-ordered on the slot's stream.
 void run_request(Request *r, cudaStream_t st) {
     AllocStream scope(st);
+    NvtxRange nvtx("server/request");
     spmv_options_t o;
     spmv_default_options(&o);
     o.precision = r->opt.mixed ? SPMV_PREC_DUAL : SPMV_PREC_FP64;
