@@ -379,6 +379,8 @@ static spmv_status_t read_scalars(spmv_matrix_t A, cudaStream_t st, CgScalars *o
 
 spmv_status_t cg_persistent64(spmv_matrix_t A, const cg_options_t &o, CgScalars *out,
                               cudaStream_t st);
+spmv_status_t cg_persistent32(spmv_matrix_t A, const cg_options_t &o, CgScalars *out,
+                              cudaStream_t st);
 
 // Plain FP64 Jacobi-PCG in the handle's x buffer; x holds x0 (or anything if !use_x0).
 static spmv_status_t solve64(spmv_matrix_t A, const double *b, const cg_options_t &o,
@@ -474,13 +476,18 @@ static spmv_status_t solve_mixed(spmv_matrix_t A, const double *b, const cg_opti
         ir_start_inner<<<G, kCgBlock, 0, st>>>(A->n, w.r.p, so, w.r32.p, w.p32.p, w.d32.p,
                                                w.dinv32.p, w.part.p, si);
         GB_LAUNCHED();
-        cudaGraphExec_t g;
-        GB_TRY(get_graph(A, true, batch, &g));
-        for (;;) {
-            GB_CUDA(cudaGraphLaunch(g, st));
-            GB_TRY(read_scalars(A, st, nullptr, &hi));
-            if (hi.done) break;
-            if (o.timeout_s > 0 && seconds_since(t0) > o.timeout_s) break;
+        if (o.persistent) {
+            GB_TRY(cg_persistent32(A, o, &hi, st));
+            if (hi.done == 4) hi.done = 0;  // timed out
+        } else {
+            cudaGraphExec_t g;
+            GB_TRY(get_graph(A, true, batch, &g));
+            for (;;) {
+                GB_CUDA(cudaGraphLaunch(g, st));
+                GB_TRY(read_scalars(A, st, nullptr, &hi));
+                if (hi.done) break;
+                if (o.timeout_s > 0 && seconds_since(t0) > o.timeout_s) break;
+            }
         }
         add_iters<<<1, 1, 0, st>>>(si, d_total);
         ir_update_x<<<G, kCgBlock, 0, st>>>(A->n, w.x.p, w.d32.p, so);

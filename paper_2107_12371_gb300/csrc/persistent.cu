@@ -1,4 +1,5 @@
-// persistent.cu -- the whole FP64 Jacobi-PCG loop in one cooperative kernel.
+// persistent.cu -- a whole Jacobi-PCG loop in one cooperative kernel (FP64 solves, and the FP32
+// inner solves of iterative refinement).
 //
 // Every CTA of a co-resident grid (cooperative launch) runs the iterations; the three phases
 // of an iteration (q = A p with p.q; x/r update with r.z and r.r; p update) are separated by a
@@ -78,11 +79,10 @@ __device__ void store_parts(double (&v)[NV], double *part) {
     }
 }
 
-template <int R, int L, typename ColT>
+template <typename T, int R, int L, typename ColT>
 __global__ void __launch_bounds__(kCgBlock, kCgCtasPerSm)
-cg_persistent(int32_t n, int32_t n_slices, const int64_t *sp, ColT col,
-              const double *val, double *x, double *r, double *p, double *q, const double *dinv,
-              double *part, CgScalars *sc) {
+cg_persistent(int32_t n, int32_t n_slices, const int64_t *sp, ColT col, const T *val, T *x,
+              T *r, T *p, T *q, const T *dinv, double *part, CgScalars *sc) {
     constexpr int S = L * R;
     const uint64_t pol = policy_evict_first();
     const long long t_start = global_timer_ns();
@@ -99,19 +99,19 @@ cg_persistent(int32_t n, int32_t n_slices, const int64_t *sp, ColT col,
     double beta = 0.0;
     while (!done) {
         // phase 1: q = A p, p.q (and CTA 0's vote to stop on the wall-clock budget)
-        double vt = 0.0;
+        T vt = T(0);
         for (int64_t g = tid; g < (int64_t)n_slices * L; g += lanes) {
             const int64_t slice = g / L;
             const int lane = (int)(g % L);
-            double acc[R];
-            slice_rows<double, R, L, true>(slice, lane, sp, col, val, p, pol, acc);
+            T acc[R];
+            slice_rows<T, R, L, true>(slice, lane, sp, col, val, p, pol, acc);
             const int64_t row0 = slice * S + (int64_t)lane * R;
-            store_rows<double, R>(q, row0, n, acc);
+            store_rows<T, R>(q, row0, n, acc);
 #pragma unroll
             for (int i = 0; i < R; ++i)
-                if (row0 + i < n) vt = fma(p[row0 + i], acc[i], vt);
+                if (row0 + i < n) vt = fma_t(p[row0 + i], acc[i], vt);
         }
-        double v1[2] = {vt, 0.0};
+        double v1[2] = {(double)vt, 0.0};
         if (blockIdx.x == 0 && threadIdx.x == 0 && budget > 0 &&
             global_timer_ns() - t_start > budget)
             v1[1] = 1.0;
@@ -130,11 +130,11 @@ cg_persistent(int32_t n, int32_t n_slices, const int64_t *sp, ColT col,
             done = 3;
             break;
         }
-        const double alpha = rho / t1[0];
+        const T alpha = (T)(rho / t1[0]);
         // phase 2: x += alpha p, r -= alpha q, r.z, r.r
-        double vz = 0.0, vr = 0.0;
-        sweep_update_xr<double>(n, alpha, x, r, p, q, dinv, vz, vr);
-        double v2[2] = {vz, vr};
+        T vz = T(0), vr = T(0);
+        sweep_update_xr<T>(n, alpha, x, r, p, q, dinv, vz, vr);
+        double v2[2] = {(double)vz, (double)vr};
         store_parts<2>(v2, part2);
         if (!grid_barrier(sc)) {
             done = 4;
@@ -153,7 +153,7 @@ cg_persistent(int32_t n, int32_t n_slices, const int64_t *sp, ColT col,
             break;
         }
         // phase 3: p = D^-1 r + beta p
-        sweep_update_p<double>(n, beta, r, dinv, p);
+        sweep_update_p<T>(n, (T)beta, r, dinv, p);
         if (!grid_barrier(sc)) {
             done = 4;
             break;
@@ -195,15 +195,18 @@ spmv_status_t diag_barrier_timeout(int ctas, double limit_s, int *done_out, cuda
     return s;
 }
 
-spmv_status_t cg_persistent64(spmv_matrix_t A, const cg_options_t &o, CgScalars *out,
-                              cudaStream_t st) {
+// One cooperative launch running the recurrence to its end; FP64 (outer scalars, FP64 work
+// vectors) or FP32 (inner scalars of the refinement, FP32 work vectors and values).
+static spmv_status_t run_persistent(spmv_matrix_t A, bool f32, const cg_options_t &o,
+                                    CgScalars *out, cudaStream_t st) {
     CgWork &w = A->cg;
-    CgScalars *sc = (CgScalars *)w.scal.p;
-    auto launch = [&](auto cols) -> spmv_status_t {
+    CgScalars *sc = (CgScalars *)w.scal.p + (f32 ? 1 : 0);
+    auto launch = [&](auto tag, auto cols) -> spmv_status_t {
+        using T = decltype(tag);
         using ColT = decltype(cols);
-        return with_shape(A->S, false, [&](auto rt, auto lt) -> spmv_status_t {
+        return with_shape(A->S, f32, [&](auto rt, auto lt) -> spmv_status_t {
             constexpr int R = decltype(rt)::value, L = decltype(lt)::value;
-            auto kern = cg_persistent<R, L, ColT>;
+            auto kern = cg_persistent<T, R, L, ColT>;
             int per_sm = 0;
             GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCgBlock, 0));
             // the grid must be co-resident and equal to the graph path's grid
@@ -214,21 +217,43 @@ spmv_status_t cg_persistent64(spmv_matrix_t A, const cg_options_t &o, CgScalars 
                                     cudaMemcpyHostToDevice, st));
             int32_t n = A->n, ns = A->n_slices;
             const int64_t *sp = A->slice_ptr.p;
-            const double *val = A->sell_val.p;
-            double *x = w.x.p, *r = w.r.p, *p = w.p.p, *q = w.q.p, *part = w.part.p;
-            const double *dinv = w.dinv.p;
+            const T *val;
+            T *x, *r, *p, *q;
+            const T *dinv;
+            if constexpr (sizeof(T) == 8) {
+                val = A->sell_val.p;
+                x = w.x.p, r = w.r.p, p = w.p.p, q = w.q.p, dinv = w.dinv.p;
+            } else {
+                val = A->sell_val32.p;
+                x = w.d32.p, r = w.r32.p, p = w.p32.p, q = w.q32.p, dinv = w.dinv32.p;
+            }
+            double *part = w.part.p;
             void *args[] = {&n, &ns, &sp, &cols, &val, &x, &r, &p, &q, &dinv, &part, &sc};
             GB_CUDA(cudaLaunchCooperativeKernel((const void *)kern, dim3(w.pers_grid),
                                                 dim3(kCgBlock), args, 0, st));
-            GB_CUDA(cudaMemcpyAsync(w.h_scal, w.scal.p, sizeof(CgScalars), cudaMemcpyDeviceToHost,
-                                    st));
+            GB_CUDA(cudaMemcpyAsync(w.h_scal, w.scal.p, 2 * sizeof(CgScalars),
+                                    cudaMemcpyDeviceToHost, st));
             GB_CUDA(cudaStreamSynchronize(st));
-            *out = w.h_scal[0];
+            *out = w.h_scal[f32 ? 1 : 0];
             return SPMV_OK;
         });
     };
-    if (A->index_bits == 16) return launch(Cols16{A->sell_col16.p, A->col_start.p});
-    return launch(Cols32{A->sell_col.p});
+    auto by_cols = [&](auto tag) -> spmv_status_t {
+        if (A->index_bits == 16) return launch(tag, Cols16{A->sell_col16.p, A->col_start.p});
+        return launch(tag, Cols32{A->sell_col.p});
+    };
+    if (f32) return by_cols(float{});
+    return by_cols(double{});
+}
+
+spmv_status_t cg_persistent64(spmv_matrix_t A, const cg_options_t &o, CgScalars *out,
+                              cudaStream_t st) {
+    return run_persistent(A, false, o, out, st);
+}
+
+spmv_status_t cg_persistent32(spmv_matrix_t A, const cg_options_t &o, CgScalars *out,
+                              cudaStream_t st) {
+    return run_persistent(A, true, o, out, st);
 }
 
 }  // namespace gb

@@ -65,6 +65,14 @@ def test_persistent_equals_graph_path(oracle, bits):
     # repeated solves are deterministic
     x3, r3 = solve(A, b, rtol=1e-10)
     assert np.array_equal(x1, x3)
+    # the FP32 inner solves of the refinement, persistent vs graph-launched
+    D = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values, index_bits=bits,
+                    precision=capi.SPMV_PREC_DUAL)
+    x4, r4 = solve(D, b, rtol=1e-10, mixed=1)
+    x5, r5 = solve(D, b, rtol=1e-10, mixed=1, persistent=1)
+    assert r4["status"] == r5["status"] == capi.SPMV_OK
+    assert (r4["iterations"], r4["outer_iterations"]) == (r5["iterations"], r5["outer_iterations"])
+    assert np.array_equal(x4, x5)
 
 
 @pytest.mark.parametrize("reorder", [capi.SPMV_REORDER_NONE, capi.SPMV_REORDER_RCM])
