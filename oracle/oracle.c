@@ -12,7 +12,7 @@
  *     slice's longest row (Sec. 4.2, ref. MON10);
  *   - per-slice first/last column of the multiplying vector (Sec. 5.1, col_start / col_end);
  *   - Jacobi-preconditioned CG and FP32-inner / FP64-outer iterative refinement (not in the
- *     paper; defined in the accompanying design notes).
+ *     paper; each is defined step by step above its routine below).
  * Compile with -O2 -ffp-contract=off so a*b+c is never fused unless fma() is called.
  *
  * Return codes: 0 ok, -1 invalid argument/matrix, -2 out of memory, 1 not converged.
