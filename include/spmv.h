@@ -289,7 +289,9 @@ typedef struct {
 spmv_status_t spmv_server_create(size_t hbm_budget_bytes, int max_slots, spmv_server_t *out);
 
 /* Enqueues a solve of A x = b (host CSR + host b, copied before return).  opt->mixed selects
- * the precision.  *ticket identifies the request.  BUDGET if it can never fit. */
+ * the precision; opt->persistent is chosen by the server (small systems run as one
+ * cooperative kernel, larger ones as CUDA-graph batches; both give identical results).
+ * *ticket identifies the request.  BUDGET if it can never fit. */
 spmv_status_t spmv_server_submit(spmv_server_t s, int32_t n, int64_t nnz, const int32_t *row_ptr,
                                  const int32_t *col_idx, const double *values, const double *b,
                                  const cg_options_t *opt, uint64_t *ticket);

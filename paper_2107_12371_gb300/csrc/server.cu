@@ -23,6 +23,7 @@
 
 namespace gb {
 void release_matrix(spmv_matrix_t A);
+int cg_grid(int32_t n);
 
 namespace {
 
@@ -99,7 +100,10 @@ void run_request(Request *r, cudaStream_t st) {
     if (s == SPMV_OK) {
         cg_options_t co = r->opt;
         co.use_x0 = 0;
-        co.persistent = 0;
+        // small systems (a grid of at most one CTA per SM) run as one cooperative kernel, which
+        // removes the launch gaps that dominate their iterations; larger ones as graph batches.
+        // Both paths give bit-identical results.
+        co.persistent = cg_grid(r->n) <= device_facts().sm_count ? 1 : 0;
         s = cg_solve(A, d_b, d_x, &co, &r->result, st);
         if (r->n > 0 && (s == SPMV_OK || s == SPMV_ERR_NOT_CONVERGED || s == SPMV_ERR_TIMEOUT)) {
             r->x.resize((size_t)r->n);
