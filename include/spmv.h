@@ -45,7 +45,8 @@ typedef enum {
     SPMV_ERR_NOT_CONVERGED = 6, /* CG reached its iteration cap                             */
     SPMV_ERR_TIMEOUT = 7,       /* a bounded device-side wait or a solve deadline expired   */
     SPMV_ERR_PENDING = 8,       /* server request not finished yet                          */
-    SPMV_ERR_UNSUPPORTED = 9    /* operation not available for this handle's precision     */
+    SPMV_ERR_UNSUPPORTED = 9,   /* operation not available for this handle's precision     */
+    SPMV_ERR_CANCELLED = 10     /* a server request was cancelled before it finished        */
 } spmv_status_t;
 
 /* reorder */
@@ -283,14 +284,22 @@ typedef struct {
     size_t bytes_in_use;     /* device bytes held by active solves             */
     size_t peak_bytes;
     double p50_latency_s, p99_latency_s; /* over completed requests               */
+    uint64_t cancelled;      /* requests that ended as SPMV_ERR_CANCELLED      */
+    /* seconds summed over finished requests, per phase on the slot threads: setup (conversion
+     * to sliced ELLPACK, copies of A and b), solve (cg_solve), teardown (copy of x, frees) */
+    double setup_s, solve_s, teardown_s;
 } spmv_server_stats_t;
 
-/* Creates a server with a device-memory budget (bytes) and at most max_slots solves in flight. */
+/* Creates a server with a device-memory budget (bytes) and at most max_slots solves in flight.
+ * The server allocates from a stream-ordered memory pool of its own that keeps up to the
+ * budget mapped after requests free it (released when the server is destroyed). */
 spmv_status_t spmv_server_create(size_t hbm_budget_bytes, int max_slots, spmv_server_t *out);
 
 /* Enqueues a solve of A x = b (host CSR + host b, copied before return).  opt->mixed selects
- * the precision; opt->persistent is chosen by the server (small systems run as one
- * cooperative kernel, larger ones as CUDA-graph batches; both give identical results).
+ * the precision; opt->persistent is ignored: the server launches every solve's kernels
+ * directly on its slot's stream, so that concurrent solves overlap on the GPU (cooperative
+ * launches from several streams do not, and a CUDA graph per one-off handle costs more to
+ * build and destroy than it saves); the result is identical either way.
  * *ticket identifies the request.  BUDGET if it can never fit. */
 spmv_status_t spmv_server_submit(spmv_server_t s, int32_t n, int64_t nnz, const int32_t *row_ptr,
                                  const int32_t *col_idx, const double *values, const double *b,
@@ -302,6 +311,15 @@ spmv_status_t spmv_server_poll(spmv_server_t s, uint64_t ticket, double *x_host,
                                cg_result_t *result);
 
 spmv_status_t spmv_server_get_stats(spmv_server_t s, spmv_server_stats_t *stats);
+
+/* Cancels a request.  A queued request never starts; a running solve stops at its next
+ * convergence check (after each CUDA-graph batch of check_every iterations; a small system
+ * running as one persistent kernel stops when that kernel returns), with none of its kernels
+ * left in flight, and frees its device memory.  Either way the request then reports
+ * SPMV_ERR_CANCELLED through poll, which leaves x_host untouched.  A request that had already
+ * finished keeps its own status.  Returns SPMV_OK for any ticket not yet polled,
+ * SPMV_ERR_INVALID_ARG otherwise.  Server-side only: no counterpart in the paper. */
+spmv_status_t spmv_server_cancel(spmv_server_t s, uint64_t ticket);
 
 /* Stops the worker, frees every request (finished or not) and the server. */
 spmv_status_t spmv_server_destroy(spmv_server_t s);

@@ -26,6 +26,7 @@ SPMV_ERR_NOT_CONVERGED = 6
 SPMV_ERR_TIMEOUT = 7
 SPMV_ERR_PENDING = 8
 SPMV_ERR_UNSUPPORTED = 9
+SPMV_ERR_CANCELLED = 10
 
 SPMV_REORDER_NONE, SPMV_REORDER_RCM, SPMV_REORDER_CM = 0, 1, 2
 SPMV_PREC_FP64, SPMV_PREC_FP32, SPMV_PREC_DUAL = 0, 1, 2
@@ -69,7 +70,9 @@ class spmv_server_stats_t(ctypes.Structure):
                 ("rejected", ctypes.c_uint64), ("active_slots", ctypes.c_int),
                 ("queued", ctypes.c_int), ("bytes_in_use", ctypes.c_size_t),
                 ("peak_bytes", ctypes.c_size_t), ("p50_latency_s", ctypes.c_double),
-                ("p99_latency_s", ctypes.c_double)]
+                ("p99_latency_s", ctypes.c_double), ("cancelled", ctypes.c_uint64),
+                ("setup_s", ctypes.c_double), ("solve_s", ctypes.c_double),
+                ("teardown_s", ctypes.c_double)]
 
 
 class SpmvError(RuntimeError):
@@ -114,6 +117,7 @@ _SIGS = {
     "spmv_server_poll": [_P, ctypes.c_uint64, _P, ctypes.POINTER(cg_result_t)],
     "spmv_server_get_stats": [_P, ctypes.POINTER(spmv_server_stats_t)],
     "spmv_server_destroy": [_P],
+    "spmv_server_cancel": [_P, ctypes.c_uint64],
 }
 
 _lib = None
@@ -353,6 +357,11 @@ def spmv_server_get_stats(s):
     stt = spmv_server_stats_t()
     _check(load().spmv_server_get_stats(s, ctypes.byref(stt)), "spmv_server_get_stats")
     return {f: getattr(stt, f) for f, _ in spmv_server_stats_t._fields_}
+
+
+def spmv_server_cancel(s, ticket):
+    """Cancel a queued or running request; its poll then reports SPMV_ERR_CANCELLED."""
+    _check(load().spmv_server_cancel(s, ctypes.c_uint64(ticket)), "spmv_server_cancel")
 
 
 def spmv_server_destroy(s):

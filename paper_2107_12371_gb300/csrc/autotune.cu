@@ -44,8 +44,8 @@ spmv_status_t autotune_matrix(spmv_matrix_t A, cudaStream_t st) {
     const size_t eb = A->has64() ? sizeof(double) : sizeof(float);
     void *x = nullptr, *y = nullptr;
     const size_t nx = (size_t)(A->n_cols > 0 ? A->n_cols : 1);
-    GB_CUDA(cudaMallocAsync(&x, eb * nx, st));
-    spmv_status_t s = cuda_status(cudaMallocAsync(&y, eb * (size_t)A->n, st));
+    GB_CUDA(gb_malloc_async(&x, eb * nx, st));
+    spmv_status_t s = cuda_status(gb_malloc_async(&y, eb * (size_t)A->n, st));
     if (s == SPMV_OK) s = cuda_status(cudaMemsetAsync(x, 0, eb * nx, st));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (s == SPMV_OK) s = cuda_status(cudaEventCreate(&e0));

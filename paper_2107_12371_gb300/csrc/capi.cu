@@ -14,6 +14,11 @@ cudaStream_t &alloc_stream() {
     return s;
 }
 
+cudaMemPool_t &alloc_pool() {
+    static thread_local cudaMemPool_t p = nullptr;
+    return p;
+}
+
 const DeviceFacts &device_facts() {
     static DeviceFacts facts[64];
     static std::mutex mu;
@@ -94,6 +99,7 @@ const char *spmv_status_string(spmv_status_t s) {
         case SPMV_ERR_TIMEOUT: return "timeout";
         case SPMV_ERR_PENDING: return "pending";
         case SPMV_ERR_UNSUPPORTED: return "unsupported for this handle";
+        case SPMV_ERR_CANCELLED: return "cancelled";
     }
     return "unknown status";
 }
@@ -129,11 +135,11 @@ spmv_status_t spmv_create(int32_t n_rows, int32_t n_cols, int64_t nnz, const int
     double *d_val = nullptr;
     spmv_status_t s = SPMV_OK;
     if (!inputs_on_device) {
-        s = cuda_status(cudaMallocAsync((void **)&d_rp, sizeof(int32_t) * ((size_t)n_rows + 1), st));
+        s = cuda_status(gb_malloc_async((void **)&d_rp, sizeof(int32_t) * ((size_t)n_rows + 1), st));
         if (s == SPMV_OK)
-            s = cuda_status(cudaMallocAsync((void **)&d_ci, sizeof(int32_t) * (nnz ? nnz : 1), st));
+            s = cuda_status(gb_malloc_async((void **)&d_ci, sizeof(int32_t) * (nnz ? nnz : 1), st));
         if (s == SPMV_OK)
-            s = cuda_status(cudaMallocAsync((void **)&d_val, sizeof(double) * (nnz ? nnz : 1), st));
+            s = cuda_status(gb_malloc_async((void **)&d_val, sizeof(double) * (nnz ? nnz : 1), st));
         if (s == SPMV_OK)
             s = cuda_status(cudaMemcpyAsync(d_rp, row_ptr, sizeof(int32_t) * ((size_t)n_rows + 1),
                                             cudaMemcpyHostToDevice, st));

@@ -11,8 +11,11 @@
 // scalars the next kernel reads.  Results therefore do not depend on CTA scheduling.  A
 // "done" flag set by that last CTA turns the remaining kernels of a CUDA-graph batch into
 // no-ops, so the host only checks convergence once per batch of iterations.
+#include <atomic>
 #include <chrono>
 #include <cmath>
+#include <mutex>
+#include <vector>
 
 #include "cgkern.cuh"
 
@@ -329,6 +332,40 @@ static spmv_status_t enqueue_residual64(spmv_matrix_t A, const double *b, bool x
     });
 }
 
+// Streams that graphs are captured on (capture needs a stream of its own: the caller's may be
+// the legacy default stream).  They live as long as the process and are shared by all
+// handles: creating and destroying a stream per handle was measured to wait behind the work
+// of other streams, stalling concurrent solves.
+struct CaptureStreams {
+    std::mutex mu;
+    std::vector<cudaStream_t> idle;
+    cudaStream_t get() {
+        {
+            std::lock_guard<std::mutex> lock(mu);
+            if (!idle.empty()) {
+                cudaStream_t s = idle.back();
+                idle.pop_back();
+                return s;
+            }
+        }
+        cudaStream_t s = nullptr;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return s;
+    }
+    void put(cudaStream_t s) {
+        std::lock_guard<std::mutex> lock(mu);
+        idle.push_back(s);
+    }
+};
+
+static CaptureStreams &capture_streams() {
+    static CaptureStreams *cs = new CaptureStreams();  // never destroyed (process lifetime)
+    return *cs;
+}
+
 // Graph of `iters` iterations, captured once per handle and kind.
 static spmv_status_t get_graph(spmv_matrix_t A, bool f32, int iters, cudaGraphExec_t *out) {
     CgWork &w = A->cg;
@@ -342,11 +379,17 @@ static spmv_status_t get_graph(spmv_matrix_t A, bool f32, int iters, cudaGraphEx
         cudaGraphExecDestroy(g);
         g = nullptr;
     }
-    if (!w.cap_stream) GB_CUDA(cudaStreamCreateWithFlags(&w.cap_stream, cudaStreamNonBlocking));
-    GB_CUDA(cudaStreamBeginCapture(w.cap_stream, cudaStreamCaptureModeThreadLocal));
-    spmv_status_t s = f32 ? enqueue_cg32(A, iters, w.cap_stream) : enqueue_cg64(A, iters, w.cap_stream);
+    cudaStream_t cs = capture_streams().get();
+    if (!cs) return SPMV_ERR_CUDA;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        capture_streams().put(cs);
+        return cuda_status(e);
+    }
+    spmv_status_t s = f32 ? enqueue_cg32(A, iters, cs) : enqueue_cg64(A, iters, cs);
     cudaGraph_t graph = nullptr;
-    cudaError_t e = cudaStreamEndCapture(w.cap_stream, &graph);
+    e = cudaStreamEndCapture(cs, &graph);
+    capture_streams().put(cs);
     if (s != SPMV_OK) {
         if (graph) cudaGraphDestroy(graph);
         return s;
@@ -364,6 +407,10 @@ using Clock = std::chrono::steady_clock;
 
 static double seconds_since(Clock::time_point t0) {
     return std::chrono::duration<double>(Clock::now() - t0).count();
+}
+
+static bool cancelled(const std::atomic<int> *cancel) {
+    return cancel && cancel->load(std::memory_order_relaxed) != 0;
 }
 
 // read both scalar blocks to the host
@@ -384,7 +431,9 @@ spmv_status_t cg_persistent32(spmv_matrix_t A, const cg_options_t &o, CgScalars 
 
 // Plain FP64 Jacobi-PCG in the handle's x buffer; x holds x0 (or anything if !use_x0).
 static spmv_status_t solve64(spmv_matrix_t A, const double *b, const cg_options_t &o,
-                             cg_result_t *res, cudaStream_t st, Clock::time_point t0) {
+                             cg_result_t *res, cudaStream_t st, Clock::time_point t0,
+                             const SolveControl &ctl) {
+    const std::atomic<int> *cancel = ctl.cancel;
     CgWork &w = A->cg;
     const int batch = o.check_every > 0 ? o.check_every : 16;
     CgScalars *sc = outer_scalars(A);
@@ -398,16 +447,21 @@ static spmv_status_t solve64(spmv_matrix_t A, const double *b, const cg_options_
         if (o.persistent) {
             GB_TRY(cg_persistent64(A, o, &h, st));
         } else {
-            cudaGraphExec_t g;
-            GB_TRY(get_graph(A, false, batch, &g));
+            cudaGraphExec_t g = nullptr;
+            if (ctl.graphs) GB_TRY(get_graph(A, false, batch, &g));
             for (;;) {
-                GB_CUDA(cudaGraphLaunch(g, st));
+                if (g) GB_CUDA(cudaGraphLaunch(g, st));
+                else GB_TRY(enqueue_cg64(A, batch, st));
                 GB_TRY(read_scalars(A, st, &h, nullptr));
-                if (h.done) break;
+                if (h.done || cancelled(cancel)) break;
                 if (o.timeout_s > 0 && seconds_since(t0) > o.timeout_s) break;
             }
         }
         total_iters = h.iters;
+        if (cancelled(cancel)) {
+            res->status = SPMV_ERR_CANCELLED;
+            break;
+        }
         if (h.done == 0 || h.done == 4) {
             res->status = SPMV_ERR_TIMEOUT;
             break;
@@ -441,7 +495,9 @@ static spmv_status_t solve64(spmv_matrix_t A, const double *b, const cg_options_
 }
 
 static spmv_status_t solve_mixed(spmv_matrix_t A, const double *b, const cg_options_t &o,
-                                 cg_result_t *res, cudaStream_t st, Clock::time_point t0) {
+                                 cg_result_t *res, cudaStream_t st, Clock::time_point t0,
+                                 const SolveControl &ctl) {
+    const std::atomic<int> *cancel = ctl.cancel;
     CgWork &w = A->cg;
     const int batch = o.check_every > 0 ? o.check_every : 16;
     const int G = cg_grid(A->n);
@@ -465,6 +521,10 @@ static spmv_status_t solve_mixed(spmv_matrix_t A, const double *b, const cg_opti
             res->status = SPMV_ERR_TIMEOUT;
             break;
         }
+        if (cancelled(cancel)) {
+            res->status = SPMV_ERR_CANCELLED;
+            break;
+        }
         // inner tolerance: inner_rtol, or (adaptive) just the reduction the outer residual
         // still needs, with a factor 2 of margin for the FP32 inner solve
         double tol_in = o.inner_rtol;
@@ -480,14 +540,19 @@ static spmv_status_t solve_mixed(spmv_matrix_t A, const double *b, const cg_opti
             GB_TRY(cg_persistent32(A, o, &hi, st));
             if (hi.done == 4) hi.done = 0;  // timed out
         } else {
-            cudaGraphExec_t g;
-            GB_TRY(get_graph(A, true, batch, &g));
+            cudaGraphExec_t g = nullptr;
+            if (ctl.graphs) GB_TRY(get_graph(A, true, batch, &g));
             for (;;) {
-                GB_CUDA(cudaGraphLaunch(g, st));
+                if (g) GB_CUDA(cudaGraphLaunch(g, st));
+                else GB_TRY(enqueue_cg32(A, batch, st));
                 GB_TRY(read_scalars(A, st, nullptr, &hi));
-                if (hi.done) break;
+                if (hi.done || cancelled(cancel)) break;
                 if (o.timeout_s > 0 && seconds_since(t0) > o.timeout_s) break;
             }
+        }
+        if (cancelled(cancel)) {
+            res->status = SPMV_ERR_CANCELLED;
+            break;
         }
         add_iters<<<1, 1, 0, st>>>(si, d_total);
         ir_update_x<<<G, kCgBlock, 0, st>>>(A->n, w.x.p, w.d32.p, so);
@@ -528,7 +593,6 @@ void release_cg(spmv_matrix_t A) {
     w.part.release(t); w.scal.release(t); w.flags.release(t);
     if (w.graph64) cudaGraphExecDestroy(w.graph64);
     if (w.graph32) cudaGraphExecDestroy(w.graph32);
-    if (w.cap_stream) cudaStreamDestroy(w.cap_stream);
     w = CgWork{};
 }
 
@@ -555,6 +619,15 @@ spmv_status_t cg_default_options(cg_options_t *o) {
 
 spmv_status_t cg_solve(spmv_matrix_t A, const double *b, double *x, const cg_options_t *opt,
                        cg_result_t *result, void *stream) {
+    return cg_solve_ex(A, b, x, opt, result, (cudaStream_t)stream, SolveControl{});
+}
+
+}  // extern "C"
+
+// cg_solve with the server's controls (cancellation flag, direct launches).
+spmv_status_t gb::cg_solve_ex(spmv_matrix_t A, const double *b, double *x,
+                              const cg_options_t *opt, cg_result_t *result, cudaStream_t st,
+                              const SolveControl &ctl) {
     if (!A) return SPMV_ERR_INVALID_ARG;
     cg_result_t local{};
     cg_result_t *res = result ? result : &local;
@@ -574,7 +647,6 @@ spmv_status_t cg_solve(spmv_matrix_t A, const double *b, double *x, const cg_opt
         res->status = SPMV_OK;
         return SPMV_OK;
     }
-    cudaStream_t st = (cudaStream_t)stream;
     AllocStream alloc_scope(st);
     NvtxRange nvtx(o.mixed ? "cg_solve/mixed" : "cg_solve/fp64");
     const auto t0 = Clock::now();
@@ -586,8 +658,12 @@ spmv_status_t cg_solve(spmv_matrix_t A, const double *b, double *x, const cg_opt
     else
         s = cuda_status(cudaMemsetAsync(w.x.p, 0, sizeof(double) * A->n, st));
     if (s != SPMV_OK) return (res->status = s);
-    s = o.mixed ? solve_mixed(A, b, o, res, st, t0) : solve64(A, b, o, res, st, t0);
+    s = o.mixed ? solve_mixed(A, b, o, res, st, t0, ctl) : solve64(A, b, o, res, st, t0, ctl);
     if (s != SPMV_OK) return (res->status = s);
+    if (res->status == SPMV_ERR_CANCELLED) {
+        s = cuda_status(cudaStreamSynchronize(st));
+        return s != SPMV_OK ? (res->status = s) : res->status;
+    }
     double rel = 0.0;
     s = final_residual(A, b, st, &rel);
     if (s != SPMV_OK) return (res->status = s);
@@ -597,5 +673,3 @@ spmv_status_t cg_solve(spmv_matrix_t A, const double *b, double *x, const cg_opt
     if (s != SPMV_OK) return (res->status = s);
     return res->status;
 }
-
-}  // extern "C"

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 
@@ -58,6 +59,21 @@ struct AllocStream {
     ~AllocStream() { alloc_stream() = saved; }
 };
 
+// Memory pool that stream-ordered allocations come from, set per host thread by AllocPool
+// (nullptr: the device's default pool).  The server gives its slot threads a pool of its own
+// whose release threshold keeps freed memory mapped, so that allocations of later requests
+// neither map nor unmap device memory.
+cudaMemPool_t &alloc_pool();
+struct AllocPool {
+    cudaMemPool_t saved;
+    explicit AllocPool(cudaMemPool_t p) : saved(alloc_pool()) { alloc_pool() = p; }
+    ~AllocPool() { alloc_pool() = saved; }
+};
+inline cudaError_t gb_malloc_async(void **p, size_t bytes, cudaStream_t st) {
+    cudaMemPool_t pool = alloc_pool();
+    return pool ? cudaMallocFromPoolAsync(p, bytes, pool, st) : cudaMallocAsync(p, bytes, st);
+}
+
 // A device allocation owned by the handle.
 template <typename T>
 struct DevBuf {
@@ -66,7 +82,7 @@ struct DevBuf {
     spmv_status_t alloc(size_t count, size_t *tally) {
         release(tally);
         if (count == 0) count = 1;
-        cudaError_t e = cudaMallocAsync((void **)&p, count * sizeof(T), alloc_stream());
+        cudaError_t e = gb_malloc_async((void **)&p, count * sizeof(T), alloc_stream());
         if (e != cudaSuccess) {
             p = nullptr;
             cudaGetLastError();
@@ -110,7 +126,6 @@ struct CgWork {
     int part_len = 0;
     bool ready = false;
     bool mixed_ready = false;
-    cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph64 = nullptr, graph32 = nullptr, graph_pers = nullptr;
     int graph64_iters = 0, graph32_iters = 0;
     int pers_grid = 0;
@@ -180,5 +195,16 @@ spmv_status_t choose_variant(spmv_matrix_t A, cudaStream_t st);
 // device scan utilities (scan.cu): exclusive prefix sum of n int64 values in place; the
 // total is written to out[n] (the array holds n + 1 entries).
 spmv_status_t exclusive_scan_i64(int64_t *d, int64_t n, cudaStream_t st);
+
+// Controls of cg_solve_ex (cg.cu); the defaults give cg_solve.
+struct SolveControl {
+    const std::atomic<int> *cancel = nullptr;  // polled at every convergence check
+    // true: each batch of iterations is a CUDA graph captured once per handle; false: the
+    // same kernels launched directly (for one-off handles: capturing, instantiating and
+    // destroying a graph per handle was measured to stall concurrent solves)
+    bool graphs = true;
+};
+spmv_status_t cg_solve_ex(spmv_matrix_t A, const double *b, double *x, const cg_options_t *opt,
+                          cg_result_t *result, cudaStream_t st, const SolveControl &ctl);
 
 }  // namespace gb

@@ -241,7 +241,7 @@ spmv_status_t cm_order_device(int32_t n, const int32_t *rp, const int32_t *ci, b
     spmv_status_t s = SPMV_OK;
     auto alloc = [&](void **p, size_t bytes) {
         if (s != SPMV_OK) return;
-        s = cuda_status(cudaMallocAsync(p, bytes, st));
+        s = cuda_status(gb_malloc_async(p, bytes, st));
     };
     alloc((void **)&w.deg, sizeof(int32_t) * n);
     alloc((void **)&w.pos, sizeof(int32_t) * n);
@@ -566,7 +566,7 @@ spmv_status_t build_sell(spmv_matrix_t A, int S, cudaStream_t st) {
     GB_TRY(A->col_start.alloc((size_t)n_slices, tally));
     GB_TRY(A->col_end.alloc((size_t)n_slices, tally));
     int *d_span = nullptr;
-    GB_CUDA(cudaMallocAsync((void **)&d_span, sizeof(int), st));
+    GB_CUDA(gb_malloc_async((void **)&d_span, sizeof(int), st));
     cudaMemsetAsync(d_span, 0, sizeof(int), st);
     window_meta<<<blocks_for((int64_t)n_slices * 32), kT, 0, st>>>(
         n_slices, S, A->slice_ptr.p, A->sell_col.p, A->col_start.p, A->col_end.p, d_span);
@@ -601,7 +601,7 @@ spmv_status_t build_matrix(spmv_matrix_t A, const int32_t *d_rp, const int32_t *
     // 1. validation
     {
         int *d_err = nullptr;
-        GB_CUDA(cudaMallocAsync((void **)&d_err, sizeof(int), st));
+        GB_CUDA(gb_malloc_async((void **)&d_err, sizeof(int), st));
         cudaMemsetAsync(d_err, 0, sizeof(int), st);
         validate_csr<<<blocks_for(n), kT, 0, st>>>(n, A->n_cols, nnz, d_rp, d_ci, d_err);
         spmv_status_t s = cuda_status(cudaGetLastError());
@@ -629,7 +629,7 @@ spmv_status_t build_matrix(spmv_matrix_t A, const int32_t *d_rp, const int32_t *
                                    A->opt.peripheral != 0, A->perm.p, st));
         if (sigma > 0) {
             int32_t *tmp = nullptr;
-            GB_CUDA(cudaMallocAsync((void **)&tmp, sizeof(int32_t) * n, st));
+            GB_CUDA(gb_malloc_async((void **)&tmp, sizeof(int32_t) * n, st));
             const unsigned windows = (unsigned)(((int64_t)n + sigma - 1) / sigma);
             sigma_sort_kernel<<<windows, 1024, sizeof(unsigned long long) * sigma, st>>>(
                 n, sigma, d_rp, reorder ? A->perm.p : nullptr, tmp);
@@ -642,8 +642,8 @@ spmv_status_t build_matrix(spmv_matrix_t A, const int32_t *d_rp, const int32_t *
         }
         int32_t *inv = nullptr;
         int64_t *len = nullptr;
-        GB_CUDA(cudaMallocAsync((void **)&inv, sizeof(int32_t) * n, st));
-        GB_CUDA(cudaMallocAsync((void **)&len, sizeof(int64_t) * ((size_t)n + 1), st));
+        GB_CUDA(gb_malloc_async((void **)&inv, sizeof(int32_t) * n, st));
+        GB_CUDA(gb_malloc_async((void **)&len, sizeof(int64_t) * ((size_t)n + 1), st));
         const unsigned nb = blocks_for(n);
         inverse_perm<<<nb, kT, 0, st>>>(n, A->perm.p, inv);
         permuted_lengths<<<nb, kT, 0, st>>>(n, d_rp, A->perm.p, len);
@@ -679,7 +679,7 @@ spmv_status_t build_matrix(spmv_matrix_t A, const int32_t *d_rp, const int32_t *
     // 4. bandwidth (reported; Sec. 4.1 defines it as the band width the reordering shrinks)
     {
         int *d_bw = nullptr;
-        GB_CUDA(cudaMallocAsync((void **)&d_bw, sizeof(int), st));
+        GB_CUDA(gb_malloc_async((void **)&d_bw, sizeof(int), st));
         cudaMemsetAsync(d_bw, 0, sizeof(int), st);
         bandwidth_kernel<<<blocks_for(n), kT, 0, st>>>(n, A->row_ptr.p, A->col.p, d_bw);
         spmv_status_t s = cuda_status(cudaGetLastError());

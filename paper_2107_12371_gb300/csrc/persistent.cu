@@ -178,7 +178,7 @@ __global__ void barrier_timeout_probe(CgScalars *sc, long long limit_ns) {
 
 spmv_status_t diag_barrier_timeout(int ctas, double limit_s, int *done_out, cudaStream_t st) {
     CgScalars *sc = nullptr;
-    GB_CUDA(cudaMallocAsync((void **)&sc, sizeof(CgScalars), st));
+    GB_CUDA(gb_malloc_async((void **)&sc, sizeof(CgScalars), st));
     spmv_status_t s = cuda_status(cudaMemsetAsync(sc, 0, sizeof(CgScalars), st));
     long long limit_ns = (long long)(limit_s * 1e9);
     void *args[] = {&sc, &limit_ns};

@@ -85,7 +85,7 @@ spmv_status_t exclusive_scan_i64(int64_t *d, int64_t n, cudaStream_t st) {
     }
     const int64_t nb = (n + kTile - 1) / kTile;
     int64_t *sums = nullptr;
-    GB_CUDA(cudaMallocAsync((void **)&sums, (size_t)(nb + 1) * sizeof(int64_t), st));
+    GB_CUDA(gb_malloc_async((void **)&sums, (size_t)(nb + 1) * sizeof(int64_t), st));
     tile_sums<<<(unsigned)nb, kThreads, 0, st>>>(d, n, sums);
     spmv_status_t s = cuda_status(cudaGetLastError());
     if (s == SPMV_OK) s = exclusive_scan_i64(sums, nb, st);

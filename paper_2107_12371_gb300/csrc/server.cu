@@ -9,6 +9,7 @@
 // host.  Every per-problem kernel uses the same fixed grid and reduction order whatever else
 // runs, so a result is bit-identical alone and in a mix.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -23,7 +24,6 @@
 
 namespace gb {
 void release_matrix(spmv_matrix_t A);
-int cg_grid(int32_t n);
 
 namespace {
 
@@ -38,8 +38,10 @@ struct Request {
     cg_options_t opt{};
     cg_result_t result{};
     spmv_status_t status = SPMV_ERR_PENDING;
+    std::atomic<int> cancel{0};
     size_t est_bytes = 0;
     Clock::time_point t_submit, t_start, t_done;
+    double setup_s = 0, solve_s = 0, teardown_s = 0;
     bool done = false;
 };
 
@@ -61,6 +63,7 @@ size_t estimate_bytes(int32_t n, int64_t nnz, bool mixed) {
 
 struct spmv_server_s {
     size_t budget = 0;
+    cudaMemPool_t pool = nullptr;  // stream-ordered allocations of the slots
     int max_slots = 1;
     int device = 0;
     std::mutex mu;
@@ -69,8 +72,9 @@ struct spmv_server_s {
     std::unordered_map<uint64_t, gb::Request *> all;
     size_t bytes_in_use = 0, peak = 0;
     int active = 0;
-    uint64_t next_ticket = 1, submitted = 0, completed = 0, rejected = 0;
+    uint64_t next_ticket = 1, submitted = 0, completed = 0, rejected = 0, cancelled = 0;
     std::vector<double> latencies;
+    double setup_s = 0, solve_s = 0, teardown_s = 0;
     std::vector<std::thread> workers;
     bool stop = false;
 };
@@ -80,9 +84,14 @@ namespace {
 
 // One solve on the slot's stream.  The handle, b and x live on the device only for its
 // duration; they are freed stream-ordered on the slot's stream.
+double since(Clock::time_point t0) {
+    return std::chrono::duration<double>(Clock::now() - t0).count();
+}
+
 void run_request(Request *r, cudaStream_t st) {
     AllocStream scope(st);
     NvtxRange nvtx("server/request");
+    auto t0 = Clock::now();
     spmv_options_t o;
     spmv_default_options(&o);
     o.precision = r->opt.mixed ? SPMV_PREC_DUAL : SPMV_PREC_FP64;
@@ -93,18 +102,27 @@ void run_request(Request *r, cudaStream_t st) {
     if (r->status != SPMV_OK) return;
     double *d_b = nullptr, *d_x = nullptr;
     const size_t vb = sizeof(double) * (size_t)(r->n > 0 ? r->n : 1);
-    spmv_status_t s = cuda_status(cudaMallocAsync((void **)&d_b, vb, st));
-    if (s == SPMV_OK) s = cuda_status(cudaMallocAsync((void **)&d_x, vb, st));
+    spmv_status_t s = cuda_status(gb_malloc_async((void **)&d_b, vb, st));
+    if (s == SPMV_OK) s = cuda_status(gb_malloc_async((void **)&d_x, vb, st));
     if (s == SPMV_OK && r->n > 0)
         s = cuda_status(cudaMemcpyAsync(d_b, r->b.data(), vb, cudaMemcpyHostToDevice, st));
+    if (s == SPMV_OK && r->cancel.load(std::memory_order_relaxed)) s = SPMV_ERR_CANCELLED;
     if (s == SPMV_OK) {
         cg_options_t co = r->opt;
         co.use_x0 = 0;
-        // small systems (a grid of at most one CTA per SM) run as one cooperative kernel, which
-        // removes the launch gaps that dominate their iterations; larger ones as graph batches.
-        // Both paths give bit-identical results.
-        co.persistent = cg_grid(r->n) <= device_facts().sm_count ? 1 : 0;
-        s = cg_solve(A, d_b, d_x, &co, &r->result, st);
+        // every solve runs as batches of separately launched kernels: those of different slot
+        // streams overlap on the GPU, whereas cooperative launches (the persistent kernel)
+        // from several streams were measured to run one after another.  All paths give
+        // bit-identical results.
+        co.persistent = 0;
+        r->setup_s = since(t0);
+        t0 = Clock::now();
+        SolveControl ctl;
+        ctl.cancel = &r->cancel;
+        ctl.graphs = false;  // a request's handle solves once: launch its kernels directly
+        s = cg_solve_ex(A, d_b, d_x, &co, &r->result, st, ctl);
+        r->solve_s = since(t0);
+        t0 = Clock::now();
         if (r->n > 0 && (s == SPMV_OK || s == SPMV_ERR_NOT_CONVERGED || s == SPMV_ERR_TIMEOUT)) {
             r->x.resize((size_t)r->n);
             spmv_status_t c =
@@ -119,10 +137,12 @@ void run_request(Request *r, cudaStream_t st) {
     if (d_x) cudaFreeAsync(d_x, st);
     release_matrix(A);
     cudaStreamSynchronize(st);
+    r->teardown_s = since(t0);
 }
 
 void worker(spmv_server_t S) {
     cudaSetDevice(S->device);
+    AllocPool pool_scope(S->pool);
     cudaStream_t st = nullptr;
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
@@ -151,8 +171,16 @@ void worker(spmv_server_t S) {
             std::lock_guard<std::mutex> lock(S->mu);
             S->bytes_in_use -= r->est_bytes;
             S->active -= 1;
-            S->completed += 1;
-            S->latencies.push_back(std::chrono::duration<double>(r->t_done - r->t_submit).count());
+            S->setup_s += r->setup_s;
+            S->solve_s += r->solve_s;
+            S->teardown_s += r->teardown_s;
+            if (r->status == SPMV_ERR_CANCELLED) {
+                S->cancelled += 1;
+            } else {
+                S->completed += 1;
+                S->latencies.push_back(
+                    std::chrono::duration<double>(r->t_done - r->t_submit).count());
+            }
             r->result.status = r->status;
             r->done = true;
         }
@@ -190,6 +218,19 @@ spmv_status_t spmv_server_create(size_t hbm_budget_bytes, int max_slots, spmv_se
         delete S;
         return SPMV_ERR_CUDA;
     }
+    // a pool of the server's own: freed blocks stay mapped up to the budget, so the next
+    // requests reuse them instead of mapping fresh memory
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = S->device;
+    if (cudaMemPoolCreate(&S->pool, &props) != cudaSuccess) {
+        cudaGetLastError();
+        delete S;
+        return SPMV_ERR_CUDA;
+    }
+    uint64_t keep = (uint64_t)hbm_budget_bytes;
+    cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &keep);
     try {
         for (int i = 0; i < max_slots; ++i) S->workers.emplace_back(worker, S);
     } catch (...) {
@@ -199,6 +240,7 @@ spmv_status_t spmv_server_create(size_t hbm_budget_bytes, int max_slots, spmv_se
         }
         S->cv.notify_all();
         for (auto &t : S->workers) t.join();
+        cudaMemPoolDestroy(S->pool);
         delete S;
         return SPMV_ERR_OOM;
     }
@@ -258,7 +300,7 @@ spmv_status_t spmv_server_poll(spmv_server_t S, uint64_t ticket, double *x_host,
         r = it->second;
         S->all.erase(it);
     }
-    if (x_host && !r->x.empty()) std::memcpy(x_host, r->x.data(), sizeof(double) * r->x.size());
+    if (x_host && !r->x.empty() && r->status != SPMV_ERR_CANCELLED) std::memcpy(x_host, r->x.data(), sizeof(double) * r->x.size());
     if (result) *result = r->result;
     const spmv_status_t s = r->status;
     delete r;
@@ -277,6 +319,35 @@ spmv_status_t spmv_server_get_stats(spmv_server_t S, spmv_server_stats_t *st) {
     st->peak_bytes = S->peak;
     st->p50_latency_s = percentile(S->latencies, 0.50);
     st->p99_latency_s = percentile(S->latencies, 0.99);
+    st->cancelled = S->cancelled;
+    st->setup_s = S->setup_s;
+    st->solve_s = S->solve_s;
+    st->teardown_s = S->teardown_s;
+    return SPMV_OK;
+}
+
+spmv_status_t spmv_server_cancel(spmv_server_t S, uint64_t ticket) {
+    if (!S) return SPMV_ERR_INVALID_ARG;
+    {
+        std::lock_guard<std::mutex> lock(S->mu);
+        auto it = S->all.find(ticket);
+        if (it == S->all.end()) return SPMV_ERR_INVALID_ARG;
+        Request *r = it->second;
+        if (r->done) return SPMV_OK;
+        auto q = std::find(S->queue.begin(), S->queue.end(), r);
+        if (q != S->queue.end()) {
+            // never started: it leaves the queue and is done at once
+            S->queue.erase(q);
+            r->status = SPMV_ERR_CANCELLED;
+            r->result.status = SPMV_ERR_CANCELLED;
+            r->t_start = r->t_done = Clock::now();
+            r->done = true;
+            S->cancelled += 1;
+        } else {
+            r->cancel.store(1, std::memory_order_relaxed);  // running: its host loop stops
+        }
+    }
+    S->cv.notify_all();  // the queue head may have changed
     return SPMV_OK;
 }
 
@@ -289,6 +360,7 @@ spmv_status_t spmv_server_destroy(spmv_server_t S) {
     S->cv.notify_all();
     for (auto &t : S->workers) t.join();
     for (auto &kv : S->all) delete kv.second;
+    cudaMemPoolDestroy(S->pool);  // every block was freed (and synchronised) by its worker
     delete S;
     return SPMV_OK;
 }

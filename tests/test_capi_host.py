@@ -48,7 +48,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_status_strings(lib):
-    for code in range(10):
+    for code in range(11):
         s = capi.spmv_status_string(code)
         assert s and s != "unknown status"
     assert capi.spmv_status_string(99) == "unknown status"
@@ -101,4 +101,5 @@ def test_entry_points_reject_null_handles(lib):
     assert L.spmv_server_submit(None, 1, 0, None, None, None, None, None, None) == \
         capi.SPMV_ERR_INVALID_ARG
     assert L.spmv_server_poll(None, 0, None, None) == capi.SPMV_ERR_INVALID_ARG
+    assert L.spmv_server_cancel(None, 0) == capi.SPMV_ERR_INVALID_ARG
     assert L.spmv_server_destroy(None) == capi.SPMV_OK

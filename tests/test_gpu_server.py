@@ -68,11 +68,25 @@ def test_alone_equals_in_mix(oracle):
     capi.spmv_server_destroy(srv)
     assert st["completed"] == len(reqs) and st["rejected"] == 0
     assert st["p99_latency_s"] >= st["p50_latency_s"] > 0
+    assert st["setup_s"] > 0 and st["solve_s"] > 0 and st["teardown_s"] > 0
     for (m, b), (xa, ra), (xm, rm) in zip(reqs, alone, mixed):
         assert ra["status"] == rm["status"] == capi.SPMV_OK
         assert np.array_equal(xa, xm)
         assert ra["iterations"] == rm["iterations"]
         assert relres(oracle, m, xm, b) <= 1e-8
+    # the server launches the kernels directly; cg_solve replays them as CUDA graphs (and the
+    # persistent kernel runs them in one launch): same kernels, same order, same bits
+    for (m, b), o, (xa, ra) in list(zip(reqs, opts, alone))[:2]:
+        A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values,
+                        precision=capi.SPMV_PREC_DUAL if o.mixed else capi.SPMV_PREC_FP64)
+        bd = torch.from_numpy(b).cuda()
+        for persistent in (0, 1):
+            xd = torch.zeros_like(bd)
+            o.persistent = persistent
+            r = capi.cg_solve(A.handle, bd, xd, o)
+            assert r["iterations"] == ra["iterations"]
+            assert np.array_equal(xd.cpu().numpy(), xa)
+        A.close()
 
 
 def test_budget_admission_and_refusal():
@@ -120,3 +134,59 @@ def test_destroy_with_requests_in_flight():
         capi.spmv_server_submit(srv, m.n, m.row_ptr, m.col_idx, m.values, b)
     capi.spmv_server_destroy(srv)  # joins the running solves, frees the queued ones
     torch.cuda.synchronize()
+
+
+def test_cancel_queued_and_running(oracle):
+    (big, bb), (small, sb), (late, lb) = requests([3e5, 2e4, 2e4], seed0=60)
+    srv = capi.spmv_server_create(8 << 30, 1)
+    # rtol 0: the big solve only ends by its (large) iteration cap, or by cancellation
+    endless = capi.cg_default_options(rtol=0.0, max_iter=200000)
+    ta = capi.spmv_server_submit(srv, big.n, big.row_ptr, big.col_idx, big.values, bb, endless)
+    tb = capi.spmv_server_submit(srv, small.n, small.row_ptr, small.col_idx, small.values, sb)
+    t0 = time.time()
+    while capi.spmv_server_get_stats(srv)["active_slots"] < 1:
+        assert time.time() - t0 < 60
+        time.sleep(0.001)
+    time.sleep(0.2)  # the big solve is in its iteration loop; the small one waits in the queue
+    st = capi.spmv_server_get_stats(srv)
+    assert st["active_slots"] == 1 and st["queued"] == 1
+    capi.spmv_server_cancel(srv, tb)  # queued: done at once
+    xb = np.full(small.n, np.nan)
+    rb = capi.spmv_server_poll(srv, tb, xb)
+    assert rb is not None and rb["status"] == capi.SPMV_ERR_CANCELLED
+    assert np.isnan(xb).all()  # x left untouched
+    capi.spmv_server_cancel(srv, ta)  # running: stops at its next convergence check
+    t1 = time.time()
+    xa = np.full(big.n, np.nan)
+    while True:
+        ra = capi.spmv_server_poll(srv, ta, xa)
+        if ra is not None:
+            break
+        assert time.time() - t1 < 30, "cancelled solve did not stop"
+        time.sleep(0.001)
+    assert ra["status"] == capi.SPMV_ERR_CANCELLED
+    assert np.isnan(xa).all()
+    st = capi.spmv_server_get_stats(srv)
+    assert st["cancelled"] == 2 and st["completed"] == 0 and st["active_slots"] == 0
+    assert st["bytes_in_use"] == 0
+    # polled tickets are gone; the server keeps serving
+    for t in (ta, tb):
+        with pytest.raises(capi.SpmvError) as e:
+            capi.spmv_server_cancel(srv, t)
+        assert e.value.status == capi.SPMV_ERR_INVALID_ARG
+    tc = capi.spmv_server_submit(srv, late.n, late.row_ptr, late.col_idx, late.values, lb,
+                                 capi.cg_default_options(rtol=1e-8))
+    (xc, rc), = wait_all(srv, [tc], [late])
+    assert rc["status"] == capi.SPMV_OK
+    assert relres(oracle, late, xc, lb) <= 1e-8
+    # cancelling a finished request that is not yet polled keeps its own status
+    td = capi.spmv_server_submit(srv, late.n, late.row_ptr, late.col_idx, late.values, lb,
+                                 capi.cg_default_options(rtol=1e-8))
+    t0 = time.time()
+    while capi.spmv_server_get_stats(srv)["completed"] < 2:
+        assert time.time() - t0 < 60
+        time.sleep(0.001)
+    capi.spmv_server_cancel(srv, td)
+    (xd, rd), = wait_all(srv, [td], [late])
+    assert rd["status"] == capi.SPMV_OK and np.array_equal(xd, xc)
+    capi.spmv_server_destroy(srv)
