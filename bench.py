@@ -611,8 +611,9 @@ def serving_results(args, capi, torch):
     """A bounded sample of the serving stream: the first n requests of the 2,000-request
     stream (cell counts log-uniform in [1e4, 2e6], seed = request index, FP64 or mixed
     precision by a seeded coin, rtol 1e-8), solved (a) one at a time through cg_solve and (b)
-    through the server with Poisson arrivals at 1x and 2x the one-at-a-time rate, 60 GB
-    budget.  Latency = arrival to result in host memory (conversion included)."""
+    through the server with Poisson arrivals at 0.5x, 1x and 2x the one-at-a-time rate, and
+    all submitted at once (its capacity), 60 GB budget.  Latency = arrival to result in host
+    memory (conversion included)."""
     import multiprocessing as mp
     from paper_2107_12371_gb300 import workloads
     n_req = args.serve_requests
@@ -636,11 +637,13 @@ def serving_results(args, capi, torch):
         lat_serial.append(time.perf_counter() - t0)
     t_serial = time.perf_counter() - t_all
     rate_serial = n_req / t_serial
-    # (b) served, Poisson arrivals at 1x and 2x the one-at-a-time rate
+    # (b) served, Poisson arrivals at 0.5x, 1x and 2x the one-at-a-time rate, and every
+    # request submitted at once (the server's capacity)
     served = {}
-    for mult in (1.0, 2.0):
-        lam = mult * rate_serial
-        gaps = np.random.default_rng(2).exponential(1.0 / lam, size=n_req)
+    for mult in (0.5, 1.0, 2.0, None):
+        lam = mult * rate_serial if mult else float("inf")
+        gaps = (np.random.default_rng(2).exponential(1.0 / lam, size=n_req) if mult
+                else np.zeros(n_req))
         srv = capi.spmv_server_create(60 << 30, args.serve_slots)
         pending = {}
         results = {}
@@ -662,10 +665,12 @@ def serving_results(args, capi, torch):
         t_served = time.perf_counter() - t0
         st = capi.spmv_server_get_stats(srv)
         capi.spmv_server_destroy(srv)
-        served["arrival_%gx" % mult] = {
-            "arrival_rate_per_s": lam, "solves_per_s": n_req / t_served,
+        served["arrival_%gx" % mult if mult else "all_at_once"] = {
+            "arrival_rate_per_s": lam if mult else None, "solves_per_s": n_req / t_served,
             "p50_latency_s": st["p50_latency_s"], "p99_latency_s": st["p99_latency_s"],
             "peak_bytes": st["peak_bytes"],
+            "phase_s": {"setup": st["setup_s"], "solve": st["solve_s"],
+                        "teardown": st["teardown_s"]},
             "converged": sum(1 for r in results.values() if r["status"] == capi.SPMV_OK),
             "max_rel_residual": max(r["rel_residual"] for r in results.values())}
     return {"serving": {

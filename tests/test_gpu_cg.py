@@ -75,6 +75,46 @@ def test_persistent_equals_graph_path(oracle, bits):
     assert np.array_equal(x4, x5)
 
 
+def tridiag(n):
+    """SPD 1-D Laplacian with a mildly varying diagonal (ragged sizes, one row per slice lane)."""
+    rows, cols, vals = [], [], []
+    for i in range(n):
+        if i > 0:
+            rows.append(i); cols.append(i - 1); vals.append(-1.0)
+        rows.append(i); cols.append(i); vals.append(2.0 + 0.01 * (i % 7))
+        if i + 1 < n:
+            rows.append(i); cols.append(i + 1); vals.append(-1.0)
+    rp = np.zeros(n + 1, np.int32)
+    np.add.at(rp, np.asarray(rows) + 1, 1)
+    return np.cumsum(rp).astype(np.int32), np.asarray(cols, np.int32), np.asarray(vals)
+
+
+@pytest.mark.parametrize("case,bits,S", [
+    ("kuhn3", 32, 64), ("kuhn12", 16, 64), ("kuhn20", 16, 64), ("kuhn26", 32, 128),
+    ("kuhn30", 16, 32), ("tri12345", 32, 256), ("tri777", 16, 64)])
+def test_persistent_equals_graph_path_shapes(oracle, case, bits, S):
+    """The cooperative persistent kernel reproduces the graph path bit for bit for grids of one
+    CTA (kuhn3) to 159 CTAs (kuhn30), ragged vector tails (tri*), every slice shape, FP64 and
+    the FP32 inner solves."""
+    if case.startswith("kuhn"):
+        m, b = workloads.kuhn(int(case[4:]), seed=7, dirichlet=True)
+        n, rp, ci, v = m.n, m.row_ptr, m.col_idx, m.values
+    else:
+        n = int(case[3:])
+        rp, ci, v = tridiag(n)
+        b = np.random.default_rng(n).uniform(-1, 1, n)
+    for prec, mixed in ((capi.SPMV_PREC_FP64, 0), (capi.SPMV_PREC_DUAL, 1)):
+        A = capi.Matrix(n, rp, ci, v, index_bits=bits, slice_height=S, precision=prec)
+        x1, r1 = solve(A, b, rtol=1e-10, mixed=mixed, max_iter=4000)
+        x2, r2 = solve(A, b, rtol=1e-10, mixed=mixed, max_iter=4000, persistent=1)
+        assert r1["status"] == r2["status"] == capi.SPMV_OK, (r1, r2)
+        assert (r1["iterations"], r1["outer_iterations"]) == (r2["iterations"],
+                                                              r2["outer_iterations"])
+        assert np.array_equal(x1, x2)
+        r = b - oracle.spmv(rp, ci, v, x2)
+        assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(b)
+
+
 @pytest.mark.parametrize("reorder", [capi.SPMV_REORDER_NONE, capi.SPMV_REORDER_RCM])
 def test_mixed_refinement_reaches_fp64_residual(oracle, reorder):
     m, b = workloads.kuhn(12, seed=1, dirichlet=True)
