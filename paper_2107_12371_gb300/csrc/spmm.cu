@@ -217,12 +217,136 @@ spmm_sell_vec(int32_t n, int32_t S, int32_t n_slices, const int64_t *__restrict_
     if (row < n) VecOf<T, VW>::store(Y + row * K + g * VW, acc);
 }
 
+// 32-byte gathers and stores of X / Y rows (256-bit accesses, sm_100 and later).
+template <typename T>
+struct Wide;
+template <>
+struct Wide<float> {
+    static constexpr int n = 8;
+    static __device__ __forceinline__ void load(const float *p, float (&v)[8]) {
+        asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+            : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]),
+              "=f"(v[7])
+            : "l"(p));
+    }
+    static __device__ __forceinline__ void store(float *p, const float (&v)[8]) {
+        asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(v[0]),
+                     "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
+                     : "memory");
+    }
+};
+template <>
+struct Wide<double> {
+    static constexpr int n = 4;
+    static __device__ __forceinline__ void load(const double *p, double (&v)[4]) {
+        asm("ld.global.nc.v4.f64 {%0,%1,%2,%3}, [%4];"
+            : "=d"(v[0]), "=d"(v[1]), "=d"(v[2]), "=d"(v[3])
+            : "l"(p));
+    }
+    static __device__ __forceinline__ void store(double *p, const double (&v)[4]) {
+        asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(p), "d"(v[0]), "d"(v[1]),
+                     "d"(v[2]), "d"(v[3])
+                     : "memory");
+    }
+};
+
+// SpMM for k = G * (32 bytes / sizeof(T)) with 32-byte aligned X and Y: lane g of a row's G
+// lanes owns 32 consecutive bytes of the row and gathers them with one 256-bit load.  Every
+// lane reads its row's (value, column) pairs itself (the G lanes of a row read the same
+// address, served by one transaction), two entries per step so that two gathers are in
+// flight, with no shuffles.  Same entry order and fused multiply-add from +0.0 as the other
+// SpMM kernels, so the results are identical.
+template <typename T, int G, typename ColT>
+__global__ void __launch_bounds__(256)
+spmm_sell_wide(int32_t n, int32_t S, int32_t n_slices, const int64_t *__restrict__ sp,
+               ColT cols, const T *__restrict__ val, const T *__restrict__ X, T *__restrict__ Y) {
+    constexpr int VW = Wide<T>::n;
+    constexpr int K = VW * G;
+    constexpr int RPW = 32 / G;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane / G, g = lane % G;
+    const int64_t rows_total = (int64_t)n_slices * S;
+    const int64_t row0 = gw * RPW;
+    if (row0 >= rows_total) return;  // whole warp: rows_total is a multiple of RPW
+    const int64_t row = row0 + sub;
+    const int64_t slice = row0 / S;
+    const int64_t r = row - slice * S;
+    const int64_t base = sp[slice];
+    const int w = (int)((sp[slice + 1] - base) / S);
+    const int32_t cbase = cols.base(slice);
+    const uint64_t pol = policy_evict_first();
+    const T *vp = val + base + r;
+    const int64_t cat = base + r;
+    const T *xg = X + g * VW;
+    T acc[VW];
+#pragma unroll
+    for (int j = 0; j < VW; ++j) acc[j] = T(0);
+    int t = 0;
+    for (; t + 2 <= w; t += 2) {
+        T a[2][1];
+        int32_t c[2][1];
+        ld_stream(vp + (int64_t)t * S, pol, a[0]);
+        cols.template load<1>(cat + (int64_t)t * S, slice, pol, cbase, c[0]);
+        ld_stream(vp + (int64_t)(t + 1) * S, pol, a[1]);
+        cols.template load<1>(cat + (int64_t)(t + 1) * S, slice, pol, cbase, c[1]);
+        T xv[2][VW];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            if (c[u][0] >= 0) Wide<T>::load(xg + (int64_t)c[u][0] * K, xv[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+            if (c[u][0] >= 0) {
+#pragma unroll
+                for (int j = 0; j < VW; ++j) acc[j] = fma_t(a[u][0], xv[u][j], acc[j]);
+            }
+    }
+    if (t < w) {
+        T a[1];
+        int32_t c[1];
+        ld_stream(vp + (int64_t)t * S, pol, a);
+        cols.template load<1>(cat + (int64_t)t * S, slice, pol, cbase, c);
+        if (c[0] >= 0) {
+            T xv[VW];
+            Wide<T>::load(xg + (int64_t)c[0] * K, xv);
+#pragma unroll
+            for (int j = 0; j < VW; ++j) acc[j] = fma_t(a[0], xv[j], acc[j]);
+        }
+    }
+    if (row < n) Wide<T>::store(Y + row * K + g * VW, acc);
+}
+
 template <typename T>
 spmv_status_t launch_spmm(spmv_matrix_t A, int k, const T *val, const T *X, T *Y,
                           cudaStream_t st) {
     if (A->n == 0) return SPMV_OK;
     const int block = 256;
     const int64_t rows_total = (int64_t)A->n_slices * A->S;
+    // 256-bit kernel when k is a power-of-two multiple of 32 bytes and X, Y allow it
+    constexpr int WV = Wide<T>::n;
+    const bool al32 = ((uintptr_t)X % 32 == 0) && ((uintptr_t)Y % 32 == 0);
+    auto wide = [&](auto gtag) -> spmv_status_t {
+        constexpr int G = decltype(gtag)::value;
+        const int64_t warps = (rows_total + (32 / G) - 1) / (32 / G);
+        const unsigned grid = grid_for(warps * 32, block);
+        if (A->index_bits == 16)
+            spmm_sell_wide<T, G, Cols16><<<grid, block, 0, st>>>(
+                A->n, A->S, A->n_slices, A->slice_ptr.p, Cols16{A->sell_col16.p, A->col_start.p},
+                val, X, Y);
+        else
+            spmm_sell_wide<T, G, Cols32><<<grid, block, 0, st>>>(
+                A->n, A->S, A->n_slices, A->slice_ptr.p, Cols32{A->sell_col.p}, val, X, Y);
+        GB_LAUNCHED();
+        return SPMV_OK;
+    };
+    if (al32) {
+        using std::integral_constant;
+        if (k == WV * 1) return wide(integral_constant<int, 1>{});
+        if (k == WV * 2) return wide(integral_constant<int, 2>{});
+        if (k == WV * 4) return wide(integral_constant<int, 4>{});
+        if (k == WV * 8) return wide(integral_constant<int, 8>{});
+    }
     // vectorised kernel when k is a power of two with k >= 16 / sizeof(T), k <= 64
     constexpr int VW = sizeof(T) == 8 ? 2 : 4;
     auto vec = [&](auto gtag) -> spmv_status_t {

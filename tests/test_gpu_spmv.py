@@ -93,6 +93,31 @@ def test_wide_slices_fall_back_to_32bit_columns(oracle):
     check_fp64(m, x, gpu_spmv(A, x), oracle)
 
 
+@pytest.mark.parametrize("span,bits", [(65534, 16), (65535, 32)])
+def test_16bit_column_boundary(oracle, span, bits):
+    """A slice spanning 65,534 columns still takes 16-bit relative columns (its largest offset,
+    65,533, is below the 0xFFFF padding mark); one more column switches the handle to 32-bit.
+    The product is exact either way, in FP64 and FP32."""
+    n = 70001  # ragged: not a multiple of the slice height
+    rng = np.random.default_rng(span)
+    rows = [np.array([0, span - 1])]
+    for i in range(1, n):
+        rows.append(np.unique(np.clip([i - 1, i, i + 1], 0, n - 1)))
+    rp = np.zeros(n + 1, np.int32)
+    rp[1:] = np.cumsum([r.size for r in rows])
+    ci = np.concatenate(rows).astype(np.int32)
+    m = meshgen.CsrMatrix(n, rp, ci, rng.uniform(-1, 1, ci.size))
+    x = rng.uniform(-1, 1, n)
+    A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values, precision=capi.SPMV_PREC_DUAL,
+                    variant=capi.SPMV_VARIANT_SELL)
+    assert A.info()["index_bits"] == bits
+    assert A.info()["max_slice_span"] == span
+    check_fp64(m, x, gpu_spmv(A, x), oracle)
+    x32 = x.astype(np.float32)
+    ref32 = oracle.spmv_f32(rp, ci, m.values.astype(np.float32), x32, use_fma=True)
+    assert np.array_equal(gpu_spmv(A, x32, f32=True), ref32)
+
+
 @pytest.mark.parametrize("precision", [capi.SPMV_PREC_FP64, capi.SPMV_PREC_FP32])
 def test_autotuned_handle_parity(oracle, precision):
     """The autotuner times every (S, CTA size, variant) candidate on the matrix and rebuilds
@@ -378,6 +403,28 @@ def test_spmm_parity(oracle, k, dtype, bits):
     c = k // 2
     yc = gpu_spmv(A, np.ascontiguousarray(X[:, c]), f32=(dtype == np.float32))
     assert np.array_equal(Y[:, c], yc)
+
+
+@pytest.mark.parametrize("k", [4, 8, 32])
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_spmm_16_byte_aligned_blocks(oracle, k, dtype):
+    """X and Y that are 16- but not 32-byte aligned take the 128-bit kernel instead of the
+    256-bit one; the product is the same."""
+    m, _ = workloads.mixed(8, k=1)
+    X = np.random.default_rng(100 + k).uniform(-1, 1, (m.n, k)).astype(dtype)
+    A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values, precision=capi.SPMV_PREC_DUAL)
+    off = 16 // np.dtype(dtype).itemsize
+    tdt = torch.float64 if dtype == np.float64 else torch.float32
+    xb = torch.zeros(m.n * k + off, dtype=tdt, device="cuda")
+    yb = torch.zeros_like(xb)
+    Xd = xb[off:].view(m.n, k)
+    Yd = yb[off:].view(m.n, k)
+    assert Xd.data_ptr() % 32 == 16 and Yd.data_ptr() % 32 == 16
+    Xd.copy_(dev(X))
+    A.apply_multi(Xd, Yd)
+    torch.cuda.synchronize()
+    ref = oracle.spmm(m.row_ptr, m.col_idx, m.values.astype(dtype), X, use_fma=True)
+    assert np.array_equal(Yd.cpu().numpy(), ref)
 
 
 # ---------------------------------------------------------------------------------------
