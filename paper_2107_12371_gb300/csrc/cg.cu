@@ -100,6 +100,14 @@ template <typename T, int R, int L, typename ColT>
 __global__ void __launch_bounds__(kCgBlock)
 cg_spmv_pq(int32_t n, int32_t n_slices, const int64_t *sp, ColT col, const T *val,
            const T *p, T *q, double *part, CgScalars *sc) {
+    // start the first slice's pointer loads while the stop flag is read, so that memory
+    // traffic begins at once (a CTA would otherwise wait a full round trip for the flag)
+    const int64_t g0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g0 < (int64_t)n_slices * L) {
+        prefetch_l1(sp + g0 / L);
+        prefetch_l1(sp + g0 / L + 1);
+        col.prefetch_base(g0 / L);
+    }
     if (sc->done) return;
     constexpr int S = L * R;
     const uint64_t pol = policy_evict_first();
@@ -133,9 +141,20 @@ template <typename T>
 __global__ void __launch_bounds__(kCgBlock)
 cg_update_xr(int32_t n, T *x, T *r, const T *p, const T *q, const T *dinv, double *part,
              CgScalars *sc) {
-    if (sc->done) return;
+    // the first vectors of the sweep and the scalars are requested together (one round trip)
+    const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * Vec16<T>::n;
+    if (i0 < n) {
+        prefetch_l1(x + i0);
+        prefetch_l1(r + i0);
+        prefetch_l1(p + i0);
+        prefetch_l1(q + i0);
+        prefetch_l1(dinv + i0);
+    }
+    const int done = sc->done;
+    const T alpha = (T)sc->alpha;
+    if (done) return;
     T vz = T(0), vr = T(0);
-    sweep_update_xr<T>(n, (T)sc->alpha, x, r, p, q, dinv, vz, vr);
+    sweep_update_xr<T>(n, alpha, x, r, p, q, dinv, vz, vr);
     double v[2] = {(double)vz, (double)vr};
     double tot[2];
     if (grid_sum_last<2>(v, part, &sc->tickets[2], tot) && threadIdx.x == 0) {
@@ -154,8 +173,16 @@ cg_update_xr(int32_t n, T *x, T *r, const T *p, const T *q, const T *dinv, doubl
 template <typename T>
 __global__ void __launch_bounds__(kCgBlock)
 cg_update_p(int32_t n, const T *r, const T *dinv, T *p, const CgScalars *sc) {
-    if (sc->done) return;
-    sweep_update_p<T>(n, (T)sc->beta, r, dinv, p);
+    const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * Vec16<T>::n;
+    if (i0 < n) {
+        prefetch_l1(r + i0);
+        prefetch_l1(dinv + i0);
+        prefetch_l1(p + i0);
+    }
+    const int done = sc->done;
+    const T beta = (T)sc->beta;
+    if (done) return;
+    sweep_update_p<T>(n, beta, r, dinv, p);
 }
 
 // refinement: right-hand side of the inner solve r32 = fp32(r64 / ||r64||), start of the
