@@ -58,3 +58,39 @@ def test_reference_arm_only_rank0_prints(tmp_path):
                        text=True, timeout=120)
     assert r.returncode == 0
     assert r.stdout.strip() == ""
+
+
+def _dying_worker(rank, world, port, q):
+    import datetime
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=5))
+    if rank == 1:
+        os._exit(0)  # the rank is lost between steps, with nothing in flight
+    try:
+        bench.reduce_max_time(1.0, world, "cpu")
+        q.put((rank, "no error"))
+    except Exception as e:  # gloo reports the lost peer instead of waiting forever
+        q.put((rank, type(e).__name__))
+
+
+def test_lost_rank_is_reported_not_hung():
+    """A rank that exits between steps: the survivor's max-over-ranks reduction ends with an
+    error within the process-group timeout instead of hanging."""
+    import time
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_dying_worker, args=(r, 2, port, q)) for r in range(2)]
+    t0 = time.time()
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+    rank, outcome = q.get(timeout=10)
+    assert rank == 0 and outcome != "no error"
+    assert time.time() - t0 < 100

@@ -190,3 +190,29 @@ def test_cancel_queued_and_running(oracle):
     (xd, rd), = wait_all(srv, [td], [late])
     assert rd["status"] == capi.SPMV_OK and np.array_equal(xd, xc)
     capi.spmv_server_destroy(srv)
+
+
+def test_bad_request_fails_alone(oracle):
+    """A request whose CSR is malformed (unsorted columns) or has no diagonal entry reports
+    INVALID_CSR; the requests around it, on the same slots, are solved as usual."""
+    (m1, b1), (m2, b2) = requests([2e4, 3e4], seed0=80)
+    bad_ci = m1.col_idx.copy()
+    lo, hi = m1.row_ptr[5], m1.row_ptr[6]
+    bad_ci[lo:hi] = bad_ci[lo:hi][::-1]  # row 5 unsorted
+    rp = np.array([0, 1, 2], np.int32)   # 2x2 without diagonal
+    srv = capi.spmv_server_create(8 << 30, 2)
+    t_good1 = capi.spmv_server_submit(srv, m1.n, m1.row_ptr, m1.col_idx, m1.values, b1)
+    t_bad = capi.spmv_server_submit(srv, m1.n, m1.row_ptr, bad_ci, m1.values, b1)
+    t_nodiag = capi.spmv_server_submit(srv, 2, rp, np.array([1, 0], np.int32), np.ones(2),
+                                       np.ones(2))
+    t_good2 = capi.spmv_server_submit(srv, m2.n, m2.row_ptr, m2.col_idx, m2.values, b2)
+    dummy = meshgen.CsrMatrix(2, rp, np.array([1, 0], np.int32), np.ones(2))
+    res = wait_all(srv, [t_good1, t_bad, t_nodiag, t_good2], [m1, m1, dummy, m2])
+    assert res[1][1]["status"] == capi.SPMV_ERR_INVALID_CSR
+    assert res[2][1]["status"] == capi.SPMV_ERR_INVALID_CSR
+    for (x, r), (m, b) in ((res[0], (m1, b1)), (res[3], (m2, b2))):
+        assert r["status"] == capi.SPMV_OK
+        assert relres(oracle, m, x, b) <= 1e-8
+    st = capi.spmv_server_get_stats(srv)
+    assert st["completed"] == 4 and st["bytes_in_use"] == 0
+    capi.spmv_server_destroy(srv)
