@@ -81,10 +81,24 @@ typedef struct {
                           * rows are sorted by decreasing length (stable) inside windows of
                           * sigma rows, so the slices pad less (the rows are renumbered: use
                           * spmv_permute / spmv_get_permutation as for a reordering). */
+    int checks;          /* 1: after the conversion, verify its structures on the device
+                          * (spmv_verify) and fail with SPMV_ERR_INVALID_CSR on any violation;
+                          * 0 = off (default).  Costs one pass over the matrix at creation. */
 } spmv_options_t;
 
+/* Invariants verified by spmv_verify, one bit each in its result:                      */
+#define SPMV_CHECK_SLICE_PTR 1  /* slice pointers start at 0, grow by multiples of S, end at
+                                 * the entry count                                         */
+#define SPMV_CHECK_ROW 2        /* each CSR row fits its slice and its columns increase    */
+#define SPMV_CHECK_COLUMN 4     /* sliced entries equal the CSR columns in [0, n_cols);
+                                 * padding is -1                                            */
+#define SPMV_CHECK_VALUE 8      /* sliced values equal the CSR values bit for bit; padding 0 */
+#define SPMV_CHECK_RANGE 16     /* every column lies in its slice's [col_start, col_end)   */
+#define SPMV_CHECK_REL16 32     /* 16-bit offsets decode to the columns; 0xFFFF = padding  */
+#define SPMV_CHECK_PERM 64      /* the renumbering is a permutation                         */
+
 /* Fills *opt with the defaults (S = 64, block = 256, AUTO variant, no reordering, FP64,
- * no autotuning, peripheral start on, automatic column index width).  Returns SPMV_ERR_INVALID_ARG if opt is NULL. */
+ * no autotuning, peripheral start on, automatic column index width, no checks).  Returns SPMV_ERR_INVALID_ARG if opt is NULL. */
 spmv_status_t spmv_default_options(spmv_options_t *opt);
 
 /* Human-readable name of a status code (static string, never NULL). */
@@ -199,6 +213,27 @@ spmv_status_t spmv_apply_chain(spmv_matrix_t B, spmv_matrix_t C, const double *x
  * elem_bytes 4 or 8; in/out device arrays of n_rows elements, must not overlap. */
 spmv_status_t spmv_permute(spmv_matrix_t A, int direction, int elem_bytes, const void *in_dev,
                            void *out_dev, void *stream);
+
+/*
+ * spmv_verify -- sync.  Verifies on the device that the handle's sliced ELLPACK arrays, slice
+ * column ranges (Sec. 5.1), 16-bit offsets and renumbering hold the invariants listed above
+ * (SPMV_CHECK_*), i.e. that every product kernel reads inside its arrays and reproduces the
+ * CSR row sums.  *violations (may be NULL) receives the bits of the violated invariants.
+ * Returns SPMV_OK when none is violated, SPMV_ERR_INVALID_CSR otherwise.  Not in the paper:
+ * a device-side substitute for a memory checker.
+ */
+spmv_status_t spmv_verify(spmv_matrix_t A, int *violations, void *stream);
+
+/*
+ * spmv_diag_checks -- sync.  Self-test of spmv_verify: plants one fault at a time in device
+ * copies of the handle's arrays (a column out of range, a changed value, a slice pointer off
+ * by one, a wrong 16-bit offset, a column range that excludes its columns, a repeated row in
+ * the renumbering; those that apply to the handle) and runs the checks on each copy.  The
+ * handle is not modified.  *planted and *detected receive one bit per fault (1, 2, 4, 8, 16,
+ * 32 in that order).  Returns SPMV_ERR_INVALID_ARG for a handle with fewer than 2 rows or no
+ * stored entry.
+ */
+spmv_status_t spmv_diag_checks(spmv_matrix_t A, int *planted, int *detected, void *stream);
 
 /* ------------------------------ conjugate gradients ------------------------------------ */
 typedef struct {

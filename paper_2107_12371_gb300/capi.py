@@ -38,7 +38,8 @@ class spmv_options_t(ctypes.Structure):
                 ("variant", ctypes.c_int), ("reorder", ctypes.c_int),
                 ("precision", ctypes.c_int), ("autotune", ctypes.c_int),
                 ("peripheral", ctypes.c_int), ("window_words", ctypes.c_int),
-                ("index_bits", ctypes.c_int), ("sigma", ctypes.c_int)]
+                ("index_bits", ctypes.c_int), ("sigma", ctypes.c_int),
+                ("checks", ctypes.c_int)]
 
 
 class spmv_info_t(ctypes.Structure):
@@ -118,6 +119,8 @@ _SIGS = {
     "spmv_server_get_stats": [_P, ctypes.POINTER(spmv_server_stats_t)],
     "spmv_server_destroy": [_P],
     "spmv_server_cancel": [_P, ctypes.c_uint64],
+    "spmv_verify": [_P, ctypes.POINTER(_int), _P],
+    "spmv_diag_checks": [_P, ctypes.POINTER(_int), ctypes.POINTER(_int), _P],
 }
 
 _lib = None
@@ -223,6 +226,23 @@ def spmv_get_info(h):
     info = spmv_info_t()
     _check(load().spmv_get_info(h, ctypes.byref(info)), "spmv_get_info")
     return {f: getattr(info, f) for f, _ in spmv_info_t._fields_}
+
+
+def spmv_verify(h, stream=None):
+    """Run the structure checks on a handle; returns the SPMV_CHECK_* bits violated (0 = none)."""
+    v = _int(0)
+    st = load().spmv_verify(h, ctypes.byref(v), _stream(stream))
+    if st not in (SPMV_OK, SPMV_ERR_INVALID_CSR):
+        raise SpmvError(st, "spmv_verify")
+    return v.value
+
+
+def spmv_diag_checks(h, stream=None):
+    """Self-test of the checks: returns (planted, detected) fault bits."""
+    p, d = _int(0), _int(0)
+    _check(load().spmv_diag_checks(h, ctypes.byref(p), ctypes.byref(d), _stream(stream)),
+           "spmv_diag_checks")
+    return p.value, d.value
 
 
 def spmv_get_permutation(h, n):

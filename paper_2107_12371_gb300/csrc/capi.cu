@@ -58,11 +58,14 @@ static spmv_status_t normalize_options(const spmv_options_t *in, spmv_options_t 
     if (o->index_bits != 0 && o->index_bits != 16 && o->index_bits != 32) return SPMV_ERR_INVALID_ARG;
     if (o->sigma != 0 && (o->sigma < 32 || o->sigma > 4096 || (o->sigma & (o->sigma - 1)) != 0))
         return SPMV_ERR_INVALID_ARG;
+    if (o->checks != 0 && o->checks != 1) return SPMV_ERR_INVALID_ARG;
     return SPMV_OK;
 }
 
 void release_matrix(spmv_matrix_t A);
 spmv_status_t autotune_matrix(spmv_matrix_t A, cudaStream_t st);
+spmv_status_t verify_matrix(spmv_matrix_t A, cudaStream_t st, int *flags);
+spmv_status_t checks_self_test(spmv_matrix_t A, cudaStream_t st, int *detected, int *planted);
 spmv_status_t diag_barrier_timeout(int ctas, double limit_s, int *done_out, cudaStream_t st);
 
 }  // namespace gb
@@ -162,6 +165,11 @@ spmv_status_t spmv_create(int32_t n_rows, int32_t n_cols, int64_t nnz, const int
     }
     if (s == SPMV_OK) s = choose_variant(A, st);
     if (s == SPMV_OK && o.autotune) s = autotune_matrix(A, st);
+    if (s == SPMV_OK && o.checks) {
+        int flags = 0;
+        s = verify_matrix(A, st, &flags);
+        if (s == SPMV_OK && flags) s = SPMV_ERR_INVALID_CSR;
+    }
     if (s == SPMV_OK) s = cuda_status(cudaStreamSynchronize(st));
     if (s != SPMV_OK) {
         cudaStreamSynchronize(st);
@@ -183,6 +191,26 @@ spmv_status_t spmv_destroy(spmv_matrix_t A) {
     }
     cudaDeviceSynchronize();
     return SPMV_OK;
+}
+
+spmv_status_t spmv_verify(spmv_matrix_t A, int *violations, void *stream) {
+    if (violations) *violations = 0;
+    if (!A) return SPMV_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    AllocStream alloc_scope(st);
+    int flags = 0;
+    GB_TRY(verify_matrix(A, st, &flags));
+    if (violations) *violations = flags;
+    return flags ? SPMV_ERR_INVALID_CSR : SPMV_OK;
+}
+
+spmv_status_t spmv_diag_checks(spmv_matrix_t A, int *planted, int *detected, void *stream) {
+    if (planted) *planted = 0;
+    if (detected) *detected = 0;
+    if (!A || !planted || !detected) return SPMV_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    AllocStream alloc_scope(st);
+    return checks_self_test(A, st, detected, planted);
 }
 
 spmv_status_t spmv_get_info(spmv_matrix_t A, spmv_info_t *info) {

@@ -81,7 +81,7 @@ def test_create_rejects_bad_arguments_before_device_work(lib):
     # bad options
     for field, value in [("slice_height", 48), ("block", 100), ("variant", 7), ("reorder", 5),
                          ("precision", 3), ("window_words", -1), ("index_bits", 8),
-                         ("sigma", 100), ("sigma", 8192)]:
+                         ("sigma", 100), ("sigma", 8192), ("checks", 2)]:
         o = capi.spmv_default_options()
         setattr(o, field, value)
         assert L.spmv_create(2, 2, 0, rp, None, None, 0, ctypes.byref(o), None,

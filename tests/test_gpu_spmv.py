@@ -428,6 +428,66 @@ def test_spmm_16_byte_aligned_blocks(oracle, k, dtype):
 
 
 # ---------------------------------------------------------------------------------------
+# structure checks (the device-side substitute for a memory checker)
+# ---------------------------------------------------------------------------------------
+CHECK_CASES = [
+    ("kuhn8", dict()),
+    ("kuhn8", dict(reorder=capi.SPMV_REORDER_RCM, precision=capi.SPMV_PREC_DUAL)),
+    ("kuhn8", dict(reorder=capi.SPMV_REORDER_RCM, sigma=64, slice_height=32, index_bits=32)),
+    ("kuhn8", dict(precision=capi.SPMV_PREC_FP32, slice_height=256)),
+    ("kuhn8", dict(variant=capi.SPMV_VARIANT_SELL_WINDOW, reorder=capi.SPMV_REORDER_CM)),
+    ("ragged", dict(slice_height=128, precision=capi.SPMV_PREC_DUAL)),
+    ("mixed", dict(reorder=capi.SPMV_REORDER_RCM, sigma=1024, precision=capi.SPMV_PREC_DUAL)),
+]
+
+
+def _check_case(name):
+    if name == "kuhn8":
+        m, _ = workloads.kuhn(8, seed=3, dirichlet=True)
+    elif name == "ragged":
+        m = ragged_matrix(3001, seed=5)
+    else:
+        m, _ = workloads.mixed(10, k=1)
+    return m
+
+
+@pytest.mark.parametrize("case", range(len(CHECK_CASES)))
+def test_checks_hold_for_every_layout(oracle, case):
+    """Handles created with checks = 1 pass the device verification of their structures for
+    every slice height, index width, precision, reordering, sigma and variant; the product is
+    unchanged."""
+    name, opts = CHECK_CASES[case]
+    m = _check_case(name)
+    A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values, checks=1, **opts)
+    assert capi.spmv_verify(A.handle) == 0
+    B = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values, **opts)  # same handle without checks
+    x = np.random.default_rng(case).uniform(-1, 1, m.n)
+    if opts.get("precision") != capi.SPMV_PREC_FP32:
+        assert np.array_equal(gpu_spmv(A, x), gpu_spmv(B, x))
+
+
+@pytest.mark.parametrize("case", [0, 1, 2, 6])
+def test_checks_detect_planted_faults(case):
+    """Each fault planted in a copy of the handle's arrays is reported by the checks (the
+    self-test covers out-of-range columns, changed values, slice pointers, 16-bit offsets,
+    column ranges and repeated rows in a renumbering)."""
+    name, opts = CHECK_CASES[case]
+    m = _check_case(name)
+    A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values, **opts)
+    planted, detected = capi.spmv_diag_checks(A.handle)
+    assert planted == detected
+    expect = 1 | 4 | 16
+    if opts.get("precision", capi.SPMV_PREC_FP64) != capi.SPMV_PREC_FP32:
+        expect |= 2
+    if A.info()["index_bits"] == 16:
+        expect |= 8
+    if opts.get("reorder", 0) != 0:
+        expect |= 32
+    assert planted == expect
+    assert capi.spmv_verify(A.handle) == 0  # the handle itself is untouched
+
+
+# ---------------------------------------------------------------------------------------
 # full size: the 6M-cell Dirichlet mesh in the benchmark's launch configuration
 # ---------------------------------------------------------------------------------------
 @pytest.mark.parametrize("reorder,bits", [(capi.SPMV_REORDER_NONE, 0),
