@@ -106,7 +106,7 @@ cg_spmv_pq(int32_t n, int32_t n_slices, const int64_t *sp, ColT col, const T *va
     if (g0 < (int64_t)n_slices * L) {
         prefetch_l1(sp + g0 / L);
         prefetch_l1(sp + g0 / L + 1);
-        col.prefetch_base(g0 / L);
+        prefetch_col_base(col, g0 / L);
     }
     if (sc->done) return;
     constexpr int S = L * R;

@@ -14,6 +14,17 @@ constexpr int kCgCtasPerSm = 4;  // at most this many CTAs per SM in a CG sweep
 
 int cg_grid(int32_t n);
 
+// Hint: bring the line holding p into L1 without waiting for it (a later load of it hits).
+__device__ __forceinline__ void prefetch_l1(const void *p) {
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
+// prefetch of a slice's column base (16-bit relative columns only)
+__device__ __forceinline__ void prefetch_col_base(const Cols32 &, int64_t) {}
+__device__ __forceinline__ void prefetch_col_base(const Cols16 &c, int64_t slice) {
+    prefetch_l1(c.col_start + slice);
+}
+
 // Sum over the CTA in a fixed tree; the total is left in every lane of warp 0.
 template <int NV>
 __device__ __forceinline__ void block_sum(double (&v)[NV]) {

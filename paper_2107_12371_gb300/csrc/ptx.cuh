@@ -136,15 +136,9 @@ __device__ __forceinline__ void ld_stream_rel16(const uint16_t *p, uint64_t pol,
     }
 }
 
-// Hint: bring the line holding p into L1 without waiting for it (a later load of it hits).
-__device__ __forceinline__ void prefetch_l1(const void *p) {
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
-}
-
 // Column indices of a slice: 32-bit absolute, or 16-bit relative to the slice's col_start.
 struct Cols32 {
     const int32_t *col;
-    __device__ __forceinline__ void prefetch_base(int64_t) const {}
     template <int R>
     __device__ __forceinline__ void load(int64_t at, int64_t, uint64_t pol, int32_t base,
                                          int32_t (&c)[R]) const {
@@ -156,9 +150,6 @@ struct Cols32 {
 struct Cols16 {
     const uint16_t *col;
     const int32_t *col_start;
-    __device__ __forceinline__ void prefetch_base(int64_t slice) const {
-        prefetch_l1(col_start + slice);
-    }
     template <int R>
     __device__ __forceinline__ void load(int64_t at, int64_t, uint64_t pol, int32_t base,
                                          int32_t (&c)[R]) const {
