@@ -515,10 +515,56 @@ def secondary(args, torch, capi, workloads, m, x, A, xi, stream, flush, dev):
     out["sell_random_order"] = timed(R, xin=xr)
     out["naive_csr_random_order"] = timed(R, csr=True, xin=xr)
     R.close()
+    out.update(table2_results(args, torch, capi, workloads, flush, stream, dev))
     out.update(cg_results(torch, capi, m, x, A, xi, dev))
     out.update(spmm_results(args, torch, capi, workloads, flush, stream, dev))
     out.update(chain_results(args, torch, capi, flush, stream, dev))
     return out
+
+
+def table2_results(args, torch, capi, workloads, flush, stream, dev):
+    """The GPU analogue of Table 2 (naive vs cached SpMV on the paper's five matrix sizes, 50K
+    to 800K tetrahedral cells): synthetic Kuhn-tet cubes of 48K-796K cells (Dirichlet, cells
+    permuted).  Per size, FP64 product times of the naive CSR kernel (x gathered from global
+    memory, Sec. 4.3) in the cells' random order and after RCM, of the sliced kernel with x
+    resident in L2, and of the sliced kernel with the circular shared-memory window of Sec.
+    5.1, both after RCM; L2 flushed before every timed step."""
+    rows = []
+    K = max(10, min(args.steps, 50))
+    for n3 in (20, 26, 32, 40, 51):
+        m, x = workloads.kuhn(n3, seed=0, dirichlet=True)
+        xd = torch.from_numpy(x).to(dev)
+        nb = spmv_bytes(m.n, m.nnz)
+
+        def ms_of(handle, xin, csr=False):
+            y = torch.empty_like(xin)
+            if csr:
+                fn = lambda: handle.apply_csr(xin, y, stream)  # noqa: E731
+            else:
+                fn = lambda: handle.apply(xin, y, stream)  # noqa: E731
+            t = sorted(time_kernel(torch, fn, K, flush, stream))
+            t = t[len(t) // 10: len(t) - len(t) // 10] or t
+            return sum(t) / len(t)
+
+        R = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values, stream=stream)
+        naive_random = ms_of(R, xd, csr=True)
+        R.close()
+        row = {"cells": m.n, "nnz": m.nnz, "naive_random_ms": naive_random}
+        for name, variant in (("cached_l2", capi.SPMV_VARIANT_SELL),
+                              ("cached_window", capi.SPMV_VARIANT_SELL_WINDOW)):
+            H = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values, stream=stream,
+                            reorder=capi.SPMV_REORDER_RCM, variant=variant)
+            xi = torch.empty_like(xd)
+            H.permute(0, xd, xi, stream)
+            if name == "cached_l2":
+                row["naive_rcm_ms"] = ms_of(H, xi, csr=True)
+            row[name + "_ms"] = ms_of(H, xi)
+            H.close()
+        row["speedup_vs_naive_random"] = row["naive_random_ms"] / row["cached_l2_ms"]
+        row["cached_l2_GBs"] = nb / (row["cached_l2_ms"] / 1e3) / 1e9
+        rows.append(row)
+    return {"table2_sizes": {"paper_speedups_for_context": [8.19, 10.95, 15.19, 15.87, 16.41],
+                             "rows": rows}}
 
 
 def cg_bytes_per_iter(n, nnz, f32=False):
