@@ -255,9 +255,11 @@ struct Wide<double> {
 // lane reads its row's (value, column) pairs itself (the G lanes of a row read the same
 // address, served by one transaction), two entries per step so that two gathers are in
 // flight, with no shuffles.  Same entry order and fused multiply-add from +0.0 as the other
-// SpMM kernels, so the results are identical.
+// SpMM kernels, so the results are identical.  FP32 products are bound by the latency of the
+// gathers and run at six CTAs per SM (40 registers; a few bytes spill), FP64 ones by the FP64
+// pipe at four.
 template <typename T, int G, typename ColT>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 4)
 spmm_sell_wide(int32_t n, int32_t S, int32_t n_slices, const int64_t *__restrict__ sp,
                ColT cols, const T *__restrict__ val, const T *__restrict__ X, T *__restrict__ Y) {
     constexpr int VW = Wide<T>::n;
