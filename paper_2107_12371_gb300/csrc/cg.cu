@@ -2,7 +2,8 @@
 // solves built on the sliced-ELLPACK product.  Neither solver is in the paper; the paper puts
 // the SpMV at the heart of the linear solver of an incompressible-flow time step (Sec. 2).
 //
-// One CG iteration is three kernels, each a grid-stride sweep over a fixed grid:
+// One CG iteration is three kernels, each a grid-stride sweep over a fixed grid (the product
+// over a grid of its own, see cg_pq_grid):
 //   cg_spmv_pq   q = A p and p.q                      -> alpha = rho / (p.q)
 //   cg_update_xr x += alpha p, r -= alpha q, r.(D^-1 r), r.r -> beta, rho, convergence
 //   cg_update_p  p = D^-1 r + beta p
@@ -95,9 +96,9 @@ cg_residual(int32_t n, int32_t n_slices, const int64_t *sp, ColT col, const T *v
     }
 }
 
-// q = A p; partial p.q; last CTA: alpha = rho / (p.q)
+// q = A p; partial p.q; last CTA: alpha = rho / (p.q).  Grid cg_pq_grid (see cgkern.cuh).
 template <typename T, int R, int L, typename ColT>
-__global__ void __launch_bounds__(kCgBlock)
+__global__ void __launch_bounds__(kCgBlock, pq_min_ctas((int)sizeof(T) * R))
 cg_spmv_pq(int32_t n, int32_t n_slices, const int64_t *sp, ColT col, const T *val,
            const T *p, T *q, double *part, CgScalars *sc) {
     // start the first slice's pointer loads while the stop flag is read, so that memory
@@ -240,6 +241,20 @@ __global__ void add_iters(CgScalars *inner, int *total) { *total += inner->iters
 // most kCgCtasPerSm CTAs per SM (the persistent kernel uses the same grid).  It depends only
 // on n and the device, so the reduction order is fixed per handle and both paths give
 // identical results; small systems use fewer CTAs and leave room for concurrent solves.
+int cg_pq_grid(int32_t n_slices, int L, int value_bytes) {
+    const int64_t cap = (int64_t)device_facts().sm_count * pq_min_ctas(value_bytes);
+    const int64_t want = ((int64_t)n_slices * L + kCgBlock - 1) / kCgBlock;
+    return (int)(want < 1 ? 1 : (want > cap ? cap : want));
+}
+
+// (lanes per slice, value bytes per lane entry) of the FP64 and FP32 product kernels for a
+// slice height, as with_shape picks them
+static int pq_grid64(const spmv_matrix_t A) { return cg_pq_grid(A->n_slices, 32, 8 * (A->S / 32)); }
+static int pq_grid32(const spmv_matrix_t A) {
+    const int L = A->S / 4 < 32 ? A->S / 4 : 32;
+    return cg_pq_grid(A->n_slices, L, 4 * (A->S / L));
+}
+
 int cg_grid(int32_t n) {
     const int cap = device_facts().sm_count * kCgCtasPerSm;
     const int64_t want = ((int64_t)n + 1023) / 1024;
@@ -253,7 +268,11 @@ spmv_status_t ensure_cg_work(spmv_matrix_t A, bool mixed, cudaStream_t st) {
     if (!w.ready) {
         const int G = cg_grid(A->n);
         w.part_len = G;
-        GB_TRY(w.part.alloc((size_t)G * kMaxParts * 2, t));
+        // the product's p.q partials (the larger of its FP64 and FP32 grids), then
+        // kMaxParts partials per CTA of the sweeps
+        const int g64 = pq_grid64(A), g32 = pq_grid32(A);
+        w.pq_len = g64 > g32 ? g64 : g32;
+        GB_TRY(w.part.alloc((size_t)w.pq_len + (size_t)G * kMaxParts * 2, t));
         GB_TRY(w.scal.alloc(2 * ((sizeof(CgScalars) + 7) / 8), t));
         GB_CUDA(cudaMemsetAsync(w.scal.p, 0, w.scal.n * sizeof(double), st));
         GB_TRY(w.flags.alloc(16, t));
@@ -305,12 +324,13 @@ static spmv_status_t enqueue_cg64(spmv_matrix_t A, int iters, cudaStream_t st) {
         using ColT = decltype(cols);
         return with_shape(A->S, false, [&](auto rt, auto lt) -> spmv_status_t {
             constexpr int R = decltype(rt)::value, L = decltype(lt)::value;
+            const int Gpq = pq_grid64(A);
             for (int it = 0; it < iters; ++it) {
-                cg_spmv_pq<double, R, L, ColT><<<G, kCgBlock, 0, st>>>(
+                cg_spmv_pq<double, R, L, ColT><<<Gpq, kCgBlock, 0, st>>>(
                     A->n, A->n_slices, A->slice_ptr.p, cols, A->sell_val.p, w.p.p, w.q.p, w.part.p,
                     sc);
                 cg_update_xr<double><<<G, kCgBlock, 0, st>>>(A->n, w.x.p, w.r.p, w.p.p, w.q.p,
-                                                             w.dinv.p, w.part.p + G, sc);
+                                                             w.dinv.p, w.part.p + w.pq_len, sc);
                 cg_update_p<double><<<G, kCgBlock, 0, st>>>(A->n, w.r.p, w.dinv.p, w.p.p, sc);
             }
             GB_LAUNCHED();
@@ -327,12 +347,14 @@ static spmv_status_t enqueue_cg32(spmv_matrix_t A, int iters, cudaStream_t st) {
         using ColT = decltype(cols);
         return with_shape(A->S, true, [&](auto rt, auto lt) -> spmv_status_t {
             constexpr int R = decltype(rt)::value, L = decltype(lt)::value;
+            const int Gpq = pq_grid32(A);
             for (int it = 0; it < iters; ++it) {
-                cg_spmv_pq<float, R, L, ColT><<<G, kCgBlock, 0, st>>>(
+                cg_spmv_pq<float, R, L, ColT><<<Gpq, kCgBlock, 0, st>>>(
                     A->n, A->n_slices, A->slice_ptr.p, cols, A->sell_val32.p, w.p32.p, w.q32.p,
                     w.part.p, sc);
                 cg_update_xr<float><<<G, kCgBlock, 0, st>>>(A->n, w.d32.p, w.r32.p, w.p32.p,
-                                                            w.q32.p, w.dinv32.p, w.part.p + G, sc);
+                                                            w.q32.p, w.dinv32.p,
+                                                            w.part.p + w.pq_len, sc);
                 cg_update_p<float><<<G, kCgBlock, 0, st>>>(A->n, w.r32.p, w.dinv32.p, w.p32.p, sc);
             }
             GB_LAUNCHED();

@@ -14,6 +14,16 @@ constexpr int kCgCtasPerSm = 4;  // at most this many CTAs per SM in a CG sweep
 
 int cg_grid(int32_t n);
 
+// The product phase q = A p, p.q runs on a grid of its own: the sweeps' grid (at most
+// kCgCtasPerSm CTAs per SM, 64 registers) leaves the latency-bound gathers without enough
+// warps, so the product takes up to pq_min_ctas CTAs per SM (40 registers where a lane
+// holds at most 16 bytes of values per entry) and at most one slice-lane per thread.  The
+// persistent kernel runs the same grid as virtual CTAs, so both paths stay bit-identical.
+constexpr int pq_min_ctas(int value_bytes) {
+    return value_bytes >= 64 ? 3 : value_bytes >= 32 ? 4 : 6;
+}
+int cg_pq_grid(int32_t n_slices, int L, int value_bytes);
+
 // Hint: bring the line holding p into L1 without waiting for it (a later load of it hits).
 __device__ __forceinline__ void prefetch_l1(const void *p) {
     asm volatile("prefetch.global.L1 [%0];" ::"l"(p));

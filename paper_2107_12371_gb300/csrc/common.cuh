@@ -124,6 +124,7 @@ struct CgWork {
     int h_flags[16] = {};       // host mirrors (read back synchronously; no pinned buffers)
     CgScalars h_scal[2] = {};
     int part_len = 0;
+    int pq_len = 0;  // leading p.q partials: one per CTA of the product grid (cg_pq_grid)
     bool ready = false;
     bool mixed_ready = false;
     cudaGraphExec_t graph64 = nullptr, graph32 = nullptr, graph_pers = nullptr;

@@ -58,14 +58,15 @@ __device__ bool grid_barrier(CgScalars *sc, unsigned expected = 0,
     return ok != 0;
 }
 
-// sum of part[k * G + i] over i in a fixed order, broadcast to all threads
+// sum of part[k * count + i] over i < count in the fixed order of grid_sum_last, broadcast
+// to all threads
 template <int NV>
-__device__ void reduce_parts(const double *part, double (&tot)[NV]) {
+__device__ void reduce_parts(const double *part, int count, double (&tot)[NV]) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
         tot[k] = 0.0;
-        for (int i = threadIdx.x; i < (int)gridDim.x; i += kCgBlock)
-            tot[k] += __ldcg(part + k * gridDim.x + i);
+        for (int i = threadIdx.x; i < count; i += kCgBlock)
+            tot[k] += __ldcg(part + (int64_t)k * count + i);
     }
     block_sum_all<NV>(tot);
 }
@@ -82,7 +83,8 @@ __device__ void store_parts(double (&v)[NV], double *part) {
 template <typename T, int R, int L, typename ColT>
 __global__ void __launch_bounds__(kCgBlock, kCgCtasPerSm)
 cg_persistent(int32_t n, int32_t n_slices, const int64_t *sp, ColT col, const T *val, T *x,
-              T *r, T *p, T *q, const T *dinv, double *part, CgScalars *sc) {
+              T *r, T *p, T *q, const T *dinv, double *part, int32_t Gpq, int32_t pq_len,
+              CgScalars *sc) {
     constexpr int S = L * R;
     const uint64_t pol = policy_evict_first();
     const long long t_start = global_timer_ns();
@@ -92,37 +94,45 @@ cg_persistent(int32_t n, int32_t n_slices, const int64_t *sp, ColT col, const T 
     int iters = sc->iters;
     const int max_iter = sc->max_iter;
     int done = sc->done;
-    double *part1 = part;                   // p.q, stop vote
-    double *part2 = part + 2 * gridDim.x;   // r.z, r.r
-    const int64_t lanes = (int64_t)gridDim.x * blockDim.x;
-    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // the product's p.q partials (one per CTA of its grid), the sweep's r.z and r.r per CTA,
+    // then CTA 0's stop vote
+    double *part1 = part;
+    double *part2 = part + pq_len;
+    double *vote = part + pq_len + 2 * gridDim.x;
+    const int64_t tasks = (int64_t)n_slices * L;
+    const int64_t pq_lanes = (int64_t)Gpq * kCgBlock;
     double beta = 0.0;
     while (!done) {
-        // phase 1: q = A p, p.q (and CTA 0's vote to stop on the wall-clock budget)
-        T vt = T(0);
-        for (int64_t g = tid; g < (int64_t)n_slices * L; g += lanes) {
-            const int64_t slice = g / L;
-            const int lane = (int)(g % L);
-            T acc[R];
-            slice_rows<T, R, L, true>(slice, lane, sp, col, val, p, pol, acc);
-            const int64_t row0 = slice * S + (int64_t)lane * R;
-            store_rows<T, R>(q, row0, n, acc);
+        // phase 1: q = A p, p.q on the product grid of the graph path (cg_pq_grid): its CTA b
+        // runs here as a virtual CTA on CTA b mod gridDim.x, with the same grid-stride order
+        // and the same CTA tree
+        for (int b = blockIdx.x; b < Gpq; b += gridDim.x) {
+            T vt = T(0);
+            for (int64_t g = (int64_t)b * kCgBlock + threadIdx.x; g < tasks; g += pq_lanes) {
+                const int64_t slice = g / L;
+                const int lane = (int)(g % L);
+                T acc[R];
+                slice_rows<T, R, L, true>(slice, lane, sp, col, val, p, pol, acc);
+                const int64_t row0 = slice * S + (int64_t)lane * R;
+                store_rows<T, R>(q, row0, n, acc);
 #pragma unroll
-            for (int i = 0; i < R; ++i)
-                if (row0 + i < n) vt = fma_t(p[row0 + i], acc[i], vt);
+                for (int i = 0; i < R; ++i)
+                    if (row0 + i < n) vt = fma_t(p[row0 + i], acc[i], vt);
+            }
+            double v1[1] = {(double)vt};
+            block_sum<1>(v1);
+            if (threadIdx.x == 0) part1[b] = v1[0];
         }
-        double v1[2] = {(double)vt, 0.0};
-        if (blockIdx.x == 0 && threadIdx.x == 0 && budget > 0 &&
-            global_timer_ns() - t_start > budget)
-            v1[1] = 1.0;
-        store_parts<2>(v1, part1);
+        // CTA 0's vote to stop on the wall-clock budget
+        if (blockIdx.x == 0 && threadIdx.x == 0)
+            vote[0] = (budget > 0 && global_timer_ns() - t_start > budget) ? 1.0 : 0.0;
         if (!grid_barrier(sc)) {
             done = 4;
             break;
         }
-        double t1[2];
-        reduce_parts<2>(part1, t1);
-        if (t1[1] != 0.0) {
+        double t1[1];
+        reduce_parts<1>(part1, Gpq, t1);
+        if (__ldcg(vote) != 0.0) {
             done = 4;
             break;
         }
@@ -141,7 +151,7 @@ cg_persistent(int32_t n, int32_t n_slices, const int64_t *sp, ColT col, const T 
             break;
         }
         double t2[2];
-        reduce_parts<2>(part2, t2);
+        reduce_parts<2>(part2, (int)gridDim.x, t2);
         beta = t2[0] / rho;
         rho = t2[0];
         ++iters;
@@ -228,7 +238,11 @@ static spmv_status_t run_persistent(spmv_matrix_t A, bool f32, const cg_options_
                 x = w.d32.p, r = w.r32.p, p = w.p32.p, q = w.q32.p, dinv = w.dinv32.p;
             }
             double *part = w.part.p;
-            void *args[] = {&n, &ns, &sp, &cols, &val, &x, &r, &p, &q, &dinv, &part, &sc};
+            // the graph path's product grid for this shape (see cg_pq_grid)
+            int32_t Gpq = cg_pq_grid(A->n_slices, L, (int)sizeof(T) * R);
+            int32_t pq_len = w.pq_len;
+            void *args[] = {&n, &ns, &sp, &cols, &val, &x, &r, &p, &q, &dinv, &part, &Gpq,
+                            &pq_len, &sc};
             GB_CUDA(cudaLaunchCooperativeKernel((const void *)kern, dim3(w.pers_grid),
                                                 dim3(kCgBlock), args, 0, st));
             GB_CUDA(cudaMemcpyAsync(w.h_scal, w.scal.p, 2 * sizeof(CgScalars),
