@@ -395,27 +395,26 @@ def run_gpu(args):
     stream.synchronize()
     e2e_serial_s = ev0.elapsed_time(ev1) / 1e3 / e2e_steps
 
-    # pipelined: step j copies its own x in and its y out, on stream j % 2 with its own device
-    # buffers, so the copies of one step overlap the product of the other (wall clock, host
-    # timer between full synchronisations)
+    # through spmv_apply_host_async: one C-ABI call per step with x and y in pinned host
+    # memory, steps alternating between two streams (and two host buffer pairs), so that
+    # consecutive calls overlap (wall clock, host timer between full synchronisations)
     streams = [stream, torch.cuda.Stream(device=dev)]
-    xs = [xi, torch.empty_like(xi)]
-    ys = [yi, torch.empty_like(yi)]
-    yhs = [yh, torch.empty(n, dtype=torch.float64).pin_memory()]
     xhs = [xh, xh.clone().pin_memory()]
+    yhs = [yh, torch.empty(n, dtype=torch.float64).pin_memory()]
 
-    def pipelined(steps):
+    def host_steps(steps):
         for j in range(steps):
-            k = j & 1
-            s_k = streams[k]
-            with torch.cuda.stream(s_k):
-                xs[k].copy_(xhs[k], non_blocking=True)
-                A.apply(xs[k], ys[k], s_k)
-                yhs[k].copy_(ys[k], non_blocking=True)
-    pipelined(4)
+            A.apply_host_async(xhs[j & 1], yhs[j & 1], streams[j & 1])
+
+    host_steps(4)
     torch.cuda.synchronize(dev)
+    # one synchronous call at a time, for comparison
     t0 = time.perf_counter()
-    pipelined(e2e_steps)
+    for _ in range(e2e_steps):
+        A.apply_host(xh, yh, stream)
+    e2e_single_s = (time.perf_counter() - t0) / e2e_steps
+    t0 = time.perf_counter()
+    host_steps(e2e_steps)
     torch.cuda.synchronize(dev)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
 
@@ -442,8 +441,12 @@ def run_gpu(args):
         "clocks": clocks,
         "e2e": {"value": nbytes / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": 8 * n,
                 "d2h_bytes_per_step": 8 * n,
-                "pipelining": "two streams: each step copies its x in and its y out; copies of "
-                              "one step overlap the product of the other",
+                "call": "spmv_apply_host_async, steps alternating between two streams "
+                        "(pinned host x and y; the copies of one call overlap the product and "
+                        "copies of the other)",
+                "one_call_at_a_time_value": nbytes / e2e_single_s / 1e9,
+                "one_call_at_a_time": "spmv_apply_host (synchronous; copy of x, product and "
+                                      "copy of y overlapped by eight runs of slices)",
                 "serial_value": nbytes / e2e_serial_s / 1e9},
         "gpu_launches": args.steps,
         "roofline": {"bound": "hbm", "achieved": nbytes / avg_launch_s / 1e9, "peak": peak,

@@ -166,6 +166,31 @@ spmv_status_t spmv_export_sell(spmv_matrix_t A, int64_t *slice_ptr, int32_t *col
  */
 spmv_status_t spmv_apply(spmv_matrix_t A, const double *x_dev, double *y_dev, void *stream);
 
+/*
+ * spmv_apply_host -- sync.  y = A x with x_host (double[n_cols]) and y_host (double[n_rows]) in
+ * host memory, internal numbering, FP64 / DUAL handles.  The rows are cut into up to 8 runs of
+ * slices; x goes to the device in increasing column order on `stream`, each run's product
+ * starts as soon as the columns its slices read (Sec. 5.1 col_end) have arrived, and its rows
+ * of y return to the host while later runs compute.  Page-locked host buffers make the copies
+ * asynchronous DMA; pageable ones work, staged by the driver.  The handle keeps device copies
+ * of x and y (counted in device_bytes) and streams of its own.  y is bit-identical to
+ * spmv_apply's.  Returns after y is on the host.  Calls on one handle from several host
+ * threads must be serialised by the caller.
+ */
+spmv_status_t spmv_apply_host(spmv_matrix_t A, const double *x_host, double *y_host,
+                              void *stream);
+
+/*
+ * spmv_apply_host_async -- async.  The same product, enqueued without waiting: `stream` reaches
+ * the end of the call's work once y_host holds the result; until then the caller must not
+ * change x_host or read y_host.  x, the product and y move in one piece each (no runs);
+ * successive calls use two device staging sets in turn, so two calls issued on different
+ * streams overlap (the copies of one with the product of the other); a staging set is reused
+ * only after its previous call is done with it.
+ */
+spmv_status_t spmv_apply_host_async(spmv_matrix_t A, const double *x_host, double *y_host,
+                                    void *stream);
+
 /* async.  y = alpha (A x) + beta y (the accumulating form of the paper's task signature, whose
  * result vector is read and written, Sec. 3.2): t = the row sum in column order, then
  * y_i = fma(alpha, t, beta * y_i), or alpha * t when beta == 0 (y is then not read, so it may

@@ -119,6 +119,8 @@ _SIGS = {
     "spmv_server_get_stats": [_P, ctypes.POINTER(spmv_server_stats_t)],
     "spmv_server_destroy": [_P],
     "spmv_server_cancel": [_P, ctypes.c_uint64],
+    "spmv_apply_host": [_P, _P, _P, _P],
+    "spmv_apply_host_async": [_P, _P, _P, _P],
     "spmv_verify": [_P, ctypes.POINTER(_int), _P],
     "spmv_diag_checks": [_P, ctypes.POINTER(_int), ctypes.POINTER(_int), _P],
 }
@@ -276,6 +278,34 @@ def spmv_apply(h, x, y, stream=None):
     _check(load().spmv_apply(h, _ptr(x), _ptr(y), _stream(stream)), "spmv_apply")
 
 
+def _host_ptr(a):
+    """Address of a host array: a C-contiguous float64 numpy array or a CPU torch tensor."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("host vectors must be C-contiguous float64")
+        return a.ctypes.data
+    if a.device.type != "cpu" or a.dtype != torch_float64() or not a.is_contiguous():
+        raise ValueError("host vectors must be contiguous float64 CPU tensors")
+    return a.data_ptr()
+
+
+def torch_float64():
+    import torch
+    return torch.float64
+
+
+def spmv_apply_host(h, x_host, y_host, stream=None):
+    """y = A x with x and y in host memory (copies pipelined with the product)."""
+    _check(load().spmv_apply_host(h, _host_ptr(x_host), _host_ptr(y_host), _stream(stream)),
+           "spmv_apply_host")
+
+
+def spmv_apply_host_async(h, x_host, y_host, stream=None):
+    """The same, enqueued on `stream` without waiting (y_host valid once the stream is done)."""
+    _check(load().spmv_apply_host_async(h, _host_ptr(x_host), _host_ptr(y_host),
+                                        _stream(stream)), "spmv_apply_host_async")
+
+
 def spmv_apply_axpby(h, alpha, x, beta, y, stream=None):
     _check(load().spmv_apply_axpby(h, float(alpha), _ptr(x), float(beta), _ptr(y),
                                    _stream(stream)), "spmv_apply_axpby")
@@ -404,6 +434,12 @@ class Matrix:
 
     def apply(self, x, y, stream=None):
         spmv_apply(self.handle, x, y, stream)
+
+    def apply_host(self, x_host, y_host, stream=None):
+        spmv_apply_host(self.handle, x_host, y_host, stream)
+
+    def apply_host_async(self, x_host, y_host, stream=None):
+        spmv_apply_host_async(self.handle, x_host, y_host, stream)
 
     def apply_f32(self, x, y, stream=None):
         spmv_apply_f32(self.handle, x, y, stream)

@@ -367,6 +367,18 @@ void release_cg(spmv_matrix_t A);
 void release_matrix(spmv_matrix_t A) {
     size_t *t = &A->bytes;
     release_cg(A);
+    for (auto &h : A->h_stage) {
+        h.x.release(t);
+        h.y.release(t);
+        for (int c = 0; c < spmv_matrix_s::kHostChunks; ++c) {
+            if (h.ev_x[c]) cudaEventDestroy(h.ev_x[c]);
+            if (h.ev_k[c]) cudaEventDestroy(h.ev_k[c]);
+        }
+        if (h.x_free) cudaEventDestroy(h.x_free);
+        if (h.y_free) cudaEventDestroy(h.y_free);
+        if (h.sk) cudaStreamDestroy(h.sk);
+        if (h.sy) cudaStreamDestroy(h.sy);
+    }
     A->perm.release(t);
     A->row_ptr.release(t);
     A->col.release(t);

@@ -428,6 +428,75 @@ def test_spmm_16_byte_aligned_blocks(oracle, k, dtype):
 
 
 # ---------------------------------------------------------------------------------------
+# products with host vectors (copies pipelined with the product inside the call)
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("case", ["kuhn_rcm", "kuhn_random", "ragged", "window", "csr",
+                                  "rect", "tiny", "pinned"])
+def test_apply_host_matches_device(oracle, case):
+    opts = {}
+    if case in ("kuhn_rcm", "window", "pinned"):
+        opts["reorder"] = capi.SPMV_REORDER_RCM
+    if case == "window":
+        opts["variant"] = capi.SPMV_VARIANT_SELL_WINDOW
+    if case == "csr":
+        opts["variant"] = capi.SPMV_VARIANT_CSR
+    n_cols = None
+    if case == "ragged":
+        m = ragged_matrix(3001, seed=8)
+        opts["slice_height"] = 128
+    elif case == "rect":
+        _, m, _, _ = meshgen.kuhn_tet_operators(5, seed=1)
+        n_cols = m.n_cols
+    elif case == "tiny":
+        m = ragged_matrix(5, seed=2, max_len=3, empty_frac=0.0)
+    else:
+        m, _ = workloads.kuhn(10, seed=6, dirichlet=True)
+    nc = n_cols if n_cols is not None else m.n
+    A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values, n_cols=n_cols, **opts)
+    rng = np.random.default_rng(len(case))
+    x = rng.uniform(-1, 1, nc)
+    if case == "pinned":
+        xh = torch.from_numpy(x).pin_memory()
+        yh = torch.full((m.n,), np.nan, dtype=torch.float64).pin_memory()
+        A.apply_host(xh, yh)
+        y_host = yh.numpy()
+    else:
+        y_host = np.full(m.n, np.nan)
+        A.apply_host(x, y_host)
+    # the device path on the same handle, and the oracle on the handle's own numbering
+    xd = dev(x)
+    yd = torch.empty(m.n, dtype=torch.float64, device="cuda")
+    A.apply(xd, yd)
+    torch.cuda.synchronize()
+    assert np.array_equal(y_host, yd.cpu().numpy())
+    rp, ci, v = capi.spmv_export_csr(A.handle, m.n, m.nnz)
+    ref = oracle.spmv(rp, ci, v, x, use_fma=True)
+    assert np.array_equal(y_host, ref)
+    # repeated calls reuse the staging and give the same bits
+    y2 = np.empty(m.n)
+    A.apply_host(x, y2)
+    assert np.array_equal(y2, y_host)
+
+
+def test_apply_host_async_overlapping_calls(oracle):
+    """Calls enqueued on two streams in turn (three calls, so the first staging set is reused
+    while the second call may still run) each deliver their own product."""
+    m, _ = workloads.kuhn(12, seed=9, dirichlet=True)
+    A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values, reorder=capi.SPMV_REORDER_RCM)
+    rp, ci, v = capi.spmv_export_csr(A.handle, m.n, m.nnz)
+    rng = np.random.default_rng(3)
+    xs = [torch.from_numpy(rng.uniform(-1, 1, m.n)).pin_memory() for _ in range(5)]
+    ys = [torch.full((m.n,), np.nan, dtype=torch.float64).pin_memory() for _ in range(5)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    for j in range(5):
+        A.apply_host_async(xs[j], ys[j], streams[j % 2])
+    torch.cuda.synchronize()
+    for j in range(5):
+        ref = oracle.spmv(rp, ci, v, xs[j].numpy(), use_fma=True)
+        assert np.array_equal(ys[j].numpy(), ref), j
+
+
+# ---------------------------------------------------------------------------------------
 # structure checks (the device-side substitute for a memory checker)
 # ---------------------------------------------------------------------------------------
 CHECK_CASES = [
