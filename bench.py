@@ -519,10 +519,65 @@ def secondary(args, torch, capi, workloads, m, x, A, xi, stream, flush, dev):
     out["naive_csr_random_order"] = timed(R, csr=True, xin=xr)
     R.close()
     out.update(table2_results(args, torch, capi, workloads, flush, stream, dev))
+    if not args.no_cpu_baseline:
+        out.update(oracle_beside_results(torch, capi, workloads, dev))
     out.update(cg_results(torch, capi, m, x, A, xi, dev))
     out.update(spmm_results(args, torch, capi, workloads, flush, stream, dev))
     out.update(chain_results(args, torch, capi, flush, stream, dev))
     return out
+
+
+def oracle_beside_results(torch, capi, workloads, dev):
+    """The CPU oracle timed beside the GPU on the same inputs for the solver rows, on bounded
+    samples (one thread, the oracle as it stands): FP64 Jacobi-PCG and mixed refinement to
+    1e-10 on the 48,000-cell Dirichlet Kuhn-tet cube, and an 8-vector SpMM on a mixed mesh of
+    about 80,000 cells.  GPU times are wall-clock per call (CG) or CUDA events (SpMM)."""
+    import oracle
+    out = {}
+    m, b = workloads.kuhn(20, seed=0, dirichlet=True)
+    A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values, precision=capi.SPMV_PREC_DUAL)
+    bd = torch.from_numpy(b).to(dev)
+    for mixed in (0, 1):
+        xd = torch.zeros_like(bd)
+        A.solve(bd, xd, raise_on_error=False, rtol=1e-10, mixed=mixed)  # warm
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        r = A.solve(bd, xd, raise_on_error=False, rtol=1e-10, mixed=mixed)
+        torch.cuda.synchronize(dev)
+        t_gpu = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        if mixed:
+            _, info = oracle.mixed_ir(m.row_ptr, m.col_idx, m.values, b, rtol=1e-10)
+            it_o = info["inner_iterations"]
+        else:
+            _, info = oracle.jacobi_pcg(m.row_ptr, m.col_idx, m.values, b, rtol=1e-10)
+            it_o = info["iterations"]
+        t_cpu = time.perf_counter() - t0
+        out["mixed_ir" if mixed else "cg_fp64"] = {
+            "cells": m.n, "gpu_s": t_gpu, "oracle_s": t_cpu, "oracle_over_gpu": t_cpu / t_gpu,
+            "gpu_iterations": r["iterations"], "oracle_iterations": it_o,
+            "gpu_rel_residual": r["rel_residual"], "oracle_rel_residual": info["rel_residual"]}
+    A.close()
+    mm, X = workloads.mixed(30, seed=1, k=8)
+    H = capi.Matrix(mm.n, mm.row_ptr, mm.col_idx, mm.values)
+    Xd = torch.from_numpy(np.ascontiguousarray(X)).to(dev)
+    Yd = torch.empty_like(Xd)
+    H.apply_multi(Xd, Yd)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record()
+    for _ in range(20):
+        H.apply_multi(Xd, Yd)
+    ev[1].record()
+    torch.cuda.synchronize(dev)
+    t_gpu = ev[0].elapsed_time(ev[1]) / 1e3 / 20
+    t0 = time.perf_counter()
+    ref = oracle.spmm(mm.row_ptr, mm.col_idx, mm.values, X, use_fma=True)
+    t_cpu = time.perf_counter() - t0
+    out["spmm_k8_fp64"] = {"cells": mm.n, "gpu_s": t_gpu, "oracle_s": t_cpu,
+                           "oracle_over_gpu": t_cpu / t_gpu,
+                           "bit_identical": bool(np.array_equal(Yd.cpu().numpy(), ref))}
+    H.close()
+    return {"oracle_beside": out}
 
 
 def table2_results(args, torch, capi, workloads, flush, stream, dev):
