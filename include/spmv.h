@@ -233,6 +233,11 @@ spmv_status_t spmv_apply_multi_f32(spmv_matrix_t A, int k, const float *X_dev, f
 spmv_status_t spmv_apply_chain(spmv_matrix_t B, spmv_matrix_t C, const double *x_dev,
                                double *y_dev, void *stream);
 
+/* async.  FP32 version of spmv_apply_chain (FP32 / DUAL handles): y equals
+ * spmv_apply_f32(B, spmv_apply_f32(C, x)) bit for bit. */
+spmv_status_t spmv_apply_chain_f32(spmv_matrix_t B, spmv_matrix_t C, const float *x_dev,
+                                   float *y_dev, void *stream);
+
 /* async.  Converts a vector between the caller's numbering and the internal one:
  * direction 0: out[new] = in[perm[new]]; direction 1: out[perm[new]] = in[new].
  * elem_bytes 4 or 8; in/out device arrays of n_rows elements, must not overlap. */

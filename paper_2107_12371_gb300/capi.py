@@ -120,6 +120,7 @@ _SIGS = {
     "spmv_server_destroy": [_P],
     "spmv_server_cancel": [_P, ctypes.c_uint64],
     "spmv_apply_host": [_P, _P, _P, _P],
+    "spmv_apply_chain_f32": [_P, _P, _P, _P, _P],
     "spmv_apply_host_async": [_P, _P, _P, _P],
     "spmv_verify": [_P, ctypes.POINTER(_int), _P],
     "spmv_diag_checks": [_P, ctypes.POINTER(_int), ctypes.POINTER(_int), _P],
@@ -323,6 +324,12 @@ def spmv_apply_f32(h, x, y, stream=None):
 def spmv_apply_chain(hb, hc, x, y, stream=None):
     """y = B (C x) without materialising C x."""
     _check(load().spmv_apply_chain(hb, hc, _ptr(x), _ptr(y), _stream(stream)), "spmv_apply_chain")
+
+
+def spmv_apply_chain_f32(hb, hc, x, y, stream=None):
+    """y = B (C x) in FP32 without writing C x (see spmv_apply_chain)."""
+    _check(load().spmv_apply_chain_f32(hb, hc, _ptr(x), _ptr(y), _stream(stream)),
+           "spmv_apply_chain_f32")
 
 
 def spmv_apply_csr(h, x, y, stream=None):

@@ -15,12 +15,12 @@
 namespace gb {
 namespace {
 
-template <int R, int L, typename ColT>
+template <typename T, int R, int L, typename ColT>
 __global__ void __launch_bounds__(1024)
 spmv_chain(int32_t n, int32_t n_slices, const int64_t *__restrict__ sp, ColT cols,
-           const double *__restrict__ bval, const int32_t *__restrict__ c_rp,
-           const int32_t *__restrict__ c_ci, const double *__restrict__ c_val,
-           const double *__restrict__ x, double *__restrict__ y) {
+           const T *__restrict__ bval, const int32_t *__restrict__ c_rp,
+           const int32_t *__restrict__ c_ci, const T *__restrict__ c_val,
+           const T *__restrict__ x, T *__restrict__ y) {
     constexpr int S = L * R;
     const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t slice = gt / L;
@@ -30,11 +30,11 @@ spmv_chain(int32_t n, int32_t n_slices, const int64_t *__restrict__ sp, ColT col
     const int w = (int)((sp[slice + 1] - base) / S);
     const int32_t cbase = cols.base(slice);
     const uint64_t pol = policy_evict_first();
-    double acc[R];
+    T acc[R];
 #pragma unroll
-    for (int i = 0; i < R; ++i) acc[i] = 0.0;
+    for (int i = 0; i < R; ++i) acc[i] = T(0);
     for (int t = 0; t < w; ++t) {
-        double v[R];
+        T v[R];
         int32_t f[R];
         ld_stream(bval + base + (int64_t)t * S + lane * R, pol, v);
         cols.template load<R>(base + (int64_t)t * S + lane * R, slice, pol, cbase, f);
@@ -42,29 +42,39 @@ spmv_chain(int32_t n, int32_t n_slices, const int64_t *__restrict__ sp, ColT col
         for (int i = 0; i < R; ++i) {
             if (f[i] < 0) continue;
             const int32_t k0 = __ldg(c_rp + f[i]), k1 = __ldg(c_rp + f[i] + 1);
-            double tf = 0.0;
-            for (int32_t k = k0; k < k1; ++k) tf = fma(__ldg(c_val + k), __ldg(x + __ldg(c_ci + k)), tf);
-            acc[i] = fma(v[i], tf, acc[i]);
+            T tf = T(0);
+            for (int32_t k = k0; k < k1; ++k)
+                tf = fma_t(__ldg(c_val + k), __ldg(x + __ldg(c_ci + k)), tf);
+            acc[i] = fma_t(v[i], tf, acc[i]);
         }
     }
-    store_rows<double, R>(y, slice * S + (int64_t)lane * R, n, acc);
+    store_rows<T, R>(y, slice * S + (int64_t)lane * R, n, acc);
 }
 
-template <int R, int L>
-spmv_status_t go_chain(spmv_matrix_t B, spmv_matrix_t C, const double *x, double *y,
-                       cudaStream_t st) {
+template <typename T, int R, int L>
+spmv_status_t go_chain(spmv_matrix_t B, spmv_matrix_t C, const T *bval, const T *cval,
+                       const T *x, T *y, cudaStream_t st) {
     const int block = 256;
     const int64_t threads = (int64_t)B->n_slices * L;
     const unsigned grid = (unsigned)((threads + block - 1) / block > 0 ? (threads + block - 1) / block : 1);
     if (B->index_bits == 16)
-        spmv_chain<R, L, Cols16><<<grid, block, 0, st>>>(
-            B->n, B->n_slices, B->slice_ptr.p, Cols16{B->sell_col16.p, B->col_start.p},
-            B->sell_val.p, C->row_ptr.p, C->col.p, C->val.p, x, y);
+        spmv_chain<T, R, L, Cols16><<<grid, block, 0, st>>>(
+            B->n, B->n_slices, B->slice_ptr.p, Cols16{B->sell_col16.p, B->col_start.p}, bval,
+            C->row_ptr.p, C->col.p, cval, x, y);
     else
-        spmv_chain<R, L, Cols32><<<grid, block, 0, st>>>(
-            B->n, B->n_slices, B->slice_ptr.p, Cols32{B->sell_col.p}, B->sell_val.p,
-            C->row_ptr.p, C->col.p, C->val.p, x, y);
+        spmv_chain<T, R, L, Cols32><<<grid, block, 0, st>>>(
+            B->n, B->n_slices, B->slice_ptr.p, Cols32{B->sell_col.p}, bval, C->row_ptr.p,
+            C->col.p, cval, x, y);
     GB_LAUNCHED();
+    return SPMV_OK;
+}
+
+spmv_status_t check_chain(spmv_matrix_t B, spmv_matrix_t C, const void *x, const void *y) {
+    if (!B || !C || B->n_cols != C->n) return SPMV_ERR_INVALID_ARG;
+    if (B->perm.p || C->perm.p) return SPMV_ERR_INVALID_ARG;  // numberings must compose as given
+    if (B->n > 0 && (!y || ((uintptr_t)y & 15u))) return SPMV_ERR_INVALID_ARG;
+    if (C->n_cols > 0 && !x) return SPMV_ERR_INVALID_ARG;
+    if (x == y) return SPMV_ERR_INVALID_ARG;
     return SPMV_OK;
 }
 
@@ -75,19 +85,32 @@ using namespace gb;
 
 extern "C" spmv_status_t spmv_apply_chain(spmv_matrix_t B, spmv_matrix_t C, const double *x,
                                           double *y, void *stream) {
-    if (!B || !C || B->n_cols != C->n) return SPMV_ERR_INVALID_ARG;
-    if (B->perm.p || C->perm.p) return SPMV_ERR_INVALID_ARG;  // numberings must compose as given
+    GB_TRY(check_chain(B, C, x, y));
     if (!B->has64() || !C->has64()) return SPMV_ERR_UNSUPPORTED;
-    if (B->n > 0 && (!y || ((uintptr_t)y & 15u))) return SPMV_ERR_INVALID_ARG;
-    if (C->n_cols > 0 && !x) return SPMV_ERR_INVALID_ARG;
-    if ((const void *)x == (const void *)y) return SPMV_ERR_INVALID_ARG;
     if (B->n == 0) return SPMV_OK;
     cudaStream_t st = (cudaStream_t)stream;
+    const double *bv = B->sell_val.p, *cv = C->val.p;
     switch (B->S) {
-        case 32: return go_chain<1, 32>(B, C, x, y, st);
-        case 64: return go_chain<2, 32>(B, C, x, y, st);
-        case 128: return go_chain<4, 32>(B, C, x, y, st);
-        case 256: return go_chain<8, 32>(B, C, x, y, st);
+        case 32: return go_chain<double, 1, 32>(B, C, bv, cv, x, y, st);
+        case 64: return go_chain<double, 2, 32>(B, C, bv, cv, x, y, st);
+        case 128: return go_chain<double, 4, 32>(B, C, bv, cv, x, y, st);
+        case 256: return go_chain<double, 8, 32>(B, C, bv, cv, x, y, st);
+    }
+    return SPMV_ERR_INVALID_ARG;
+}
+
+extern "C" spmv_status_t spmv_apply_chain_f32(spmv_matrix_t B, spmv_matrix_t C, const float *x,
+                                              float *y, void *stream) {
+    GB_TRY(check_chain(B, C, x, y));
+    if (!B->has32() || !C->has32()) return SPMV_ERR_UNSUPPORTED;
+    if (B->n == 0) return SPMV_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const float *bv = B->sell_val32.p, *cv = C->val32.p;
+    switch (B->S) {  // (R, L) of the FP32 sliced kernels
+        case 32: return go_chain<float, 4, 8>(B, C, bv, cv, x, y, st);
+        case 64: return go_chain<float, 4, 16>(B, C, bv, cv, x, y, st);
+        case 128: return go_chain<float, 4, 32>(B, C, bv, cv, x, y, st);
+        case 256: return go_chain<float, 8, 32>(B, C, bv, cv, x, y, st);
     }
     return SPMV_ERR_INVALID_ARG;
 }

@@ -221,6 +221,23 @@ def test_rectangular_operators_parity(oracle):
         capi.spmv_apply_chain(Ms.handle, Gh.handle, xd, yc)
         torch.cuda.synchronize()
         assert np.array_equal(yc.cpu().numpy(), ref_y), S
+    # the FP32 chain equals the two FP32 products and the FP32 oracle, bit for bit
+    G32 = capi.Matrix(G.n, G.row_ptr, G.col_idx, G.values, n_cols=G.n_cols,
+                      precision=capi.SPMV_PREC_FP32)
+    x32 = x.astype(np.float32)
+    ref_g32 = oracle.spmv_f32(G.row_ptr, G.col_idx, G.values.astype(np.float32), x32)
+    ref_y32 = oracle.spmv_f32(M.row_ptr, M.col_idx, M.values.astype(np.float32), ref_g32)
+    for S in (32, 64, 128, 256):
+        M32 = capi.Matrix(M.n, M.row_ptr, M.col_idx, M.values, n_cols=M.n_cols, slice_height=S,
+                          precision=capi.SPMV_PREC_DUAL)
+        y32 = torch.empty(M.n, dtype=torch.float32, device="cuda")
+        capi.spmv_apply_chain_f32(M32.handle, G32.handle, dev(x32), y32)
+        torch.cuda.synchronize()
+        assert np.array_equal(y32.cpu().numpy(), ref_y32), S
+    with pytest.raises(capi.SpmvError) as e:  # an FP64-only handle has no FP32 values
+        capi.spmv_apply_chain_f32(Mh.handle, G32.handle, dev(x32),
+                                  torch.empty(M.n, dtype=torch.float32, device="cuda"))
+    assert e.value.status == capi.SPMV_ERR_UNSUPPORTED
     # rectangular matrices cannot be renumbered symmetrically, nor solved by CG
     st, h = capi.spmv_create(G.n, G.row_ptr, G.col_idx, G.values, raw_status=True, n_cols=L.n,
                              options=capi.spmv_default_options(reorder=capi.SPMV_REORDER_RCM))
