@@ -495,8 +495,23 @@ def secondary(args, torch, capi, workloads, m, x, A, xi, stream, flush, dev):
         return {"value": nb / (ms / 1e3) / 1e9, "unit": "GB/s", "ms": ms}
 
     # FP32 product (the mixed-precision inner SpMV) of the headline handle, whose layout was
-    # tuned for the FP64 product
+    # tuned for the FP64 product; its error against the FP64 product (which equals the FP64
+    # oracle bit for bit), normwise and per entry relative to sum_j |a_ij x_j|
     out["fp32_spmv"] = dict(timed(A, f32=True), algorithmic_bytes=nb32)
+    y64 = torch.empty_like(xi)
+    A.apply(xi, y64, stream)
+    y32 = torch.empty(n, dtype=torch.float32, device=dev)
+    A.apply_f32(xi.float(), y32, stream)
+    absA = torch.empty_like(xi)
+    Aabs = capi.Matrix(n, m.row_ptr, m.col_idx, np.abs(m.values), stream=stream,
+                       reorder=capi.SPMV_REORDER_RCM)
+    Aabs.apply(xi.abs(), absA, stream)  # same renumbering: RCM of the same pattern
+    Aabs.close()
+    torch.cuda.synchronize(dev)
+    d = (y32.double() - y64).abs()
+    out["fp32_spmv"]["error_vs_fp64"] = {
+        "normwise": float(d.norm() / y64.norm()),
+        "max_componentwise": float((d / absA.clamp_min(1e-300)).max())}
     # an FP32 handle of the same matrix with its layout tuned for the FP32 product
     F = capi.Matrix(n, m.row_ptr, m.col_idx, m.values, stream=stream,
                     reorder=capi.SPMV_REORDER_RCM, precision=capi.SPMV_PREC_FP32, autotune=1)
@@ -562,13 +577,16 @@ def oracle_beside_results(torch, capi, workloads, dev):
             _, info = oracle.mixed_ir(m.row_ptr, m.col_idx, m.values, b, rtol=1e-10)
             it_o = info["inner_iterations"]
         else:
-            _, info = oracle.jacobi_pcg(m.row_ptr, m.col_idx, m.values, b, rtol=1e-10)
+            x64_oracle, info = oracle.jacobi_pcg(m.row_ptr, m.col_idx, m.values, b, rtol=1e-10)
             it_o = info["iterations"]
         t_cpu = time.perf_counter() - t0
+        xg = xd.cpu().numpy()
         out["mixed_ir" if mixed else "cg_fp64"] = {
             "cells": m.n, "gpu_s": t_gpu, "oracle_s": t_cpu, "oracle_over_gpu": t_cpu / t_gpu,
             "gpu_iterations": r["iterations"], "oracle_iterations": it_o,
-            "gpu_rel_residual": r["rel_residual"], "oracle_rel_residual": info["rel_residual"]}
+            "gpu_rel_residual": r["rel_residual"], "oracle_rel_residual": info["rel_residual"],
+            "error_vs_fp64_oracle": float(np.linalg.norm(xg - x64_oracle) /
+                                          np.linalg.norm(x64_oracle))}
     A.close()
     mm, X = workloads.mixed(30, seed=1, k=8)
     H = capi.Matrix(mm.n, mm.row_ptr, mm.col_idx, mm.values)
