@@ -172,7 +172,7 @@ spmv_status_t spmv_apply(spmv_matrix_t A, const double *x_dev, double *y_dev, vo
  * slices; x goes to the device in increasing column order on `stream`, each run's product
  * starts as soon as the columns its slices read (Sec. 5.1 col_end) have arrived, and its rows
  * of y return to the host while later runs compute.  Page-locked host buffers make the copies
- * asynchronous DMA; pageable ones work, staged by the driver.  The handle keeps device copies
+ * asynchronous DMA; pageable ones work, staged by the CUDA runtime.  The handle keeps device copies
  * of x and y (counted in device_bytes) and streams of its own.  y is bit-identical to
  * spmv_apply's.  Returns after y is on the host.  Calls on one handle from several host
  * threads must be serialised by the caller.
