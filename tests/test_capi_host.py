@@ -102,4 +102,9 @@ def test_entry_points_reject_null_handles(lib):
         capi.SPMV_ERR_INVALID_ARG
     assert L.spmv_server_poll(None, 0, None, None) == capi.SPMV_ERR_INVALID_ARG
     assert L.spmv_server_cancel(None, 0) == capi.SPMV_ERR_INVALID_ARG
+    assert L.spmv_apply_host(None, None, None, None) == capi.SPMV_ERR_INVALID_ARG
+    assert L.spmv_apply_host_async(None, None, None, None) == capi.SPMV_ERR_INVALID_ARG
+    assert L.spmv_apply_chain_f32(None, None, None, None, None) == capi.SPMV_ERR_INVALID_ARG
+    assert L.spmv_verify(None, None, None) == capi.SPMV_ERR_INVALID_ARG
+    assert L.spmv_diag_checks(None, None, None, None) == capi.SPMV_ERR_INVALID_ARG
     assert L.spmv_server_destroy(None) == capi.SPMV_OK
