@@ -506,6 +506,44 @@ def test_pcg_zero_rhs_and_iteration_cap(oracle):
     assert not info["converged"] and info["iterations"] == 3
 
 
+def test_pcg_energy_error_decreases_monotonically(oracle):
+    """Preconditioned CG minimises the A-norm of the error over a growing Krylov space, so
+    ||x_k - x*||_A never increases from one iteration to the next and, in exact arithmetic,
+    reaches zero within n steps.  The iterates are the oracle's runs capped at k iterations.
+    A wrong step length or direction update (alpha, beta, the preconditioner) breaks this."""
+    m, rng = meshgen.kuhn_tet_matrix(3, seed=5, dirichlet=True)
+    b = meshgen.uniform_vectors(rng, m.n)
+    A = m.to_dense()
+    xs = np.linalg.solve(A, b)
+
+    def energy(x):
+        e = x - xs
+        return float(e @ (A @ e))
+
+    prev = energy(np.zeros(m.n))
+    for k in range(1, 40):
+        x, info = oracle.jacobi_pcg(m.row_ptr, m.col_idx, m.values, b, rtol=0.0, max_iter=k,
+                                    max_restarts=0)
+        assert info["iterations"] == k
+        e = energy(x)
+        assert e <= prev * (1 + 1e-9) + 1e-28, k
+        prev = e
+    assert prev <= 1e-16 * energy(np.zeros(m.n))  # converged to rounding (error ~1e-9)
+
+
+def test_mixed_ir_outer_steps_contract(oracle):
+    """Each refinement step solves A d = r to the inner tolerance, so the outer residual falls
+    by about that factor per step: with a fixed inner tolerance of 1e-3, reaching 1e-10 takes
+    at most ceil(10 / 3) + 1 = 5 steps and at least 2 (an FP32 inner solve cannot give 1e-10)."""
+    m, rng = meshgen.kuhn_tet_matrix(5, seed=2, dirichlet=True)
+    b = meshgen.uniform_vectors(rng, m.n)
+    x, info = oracle.mixed_ir(m.row_ptr, m.col_idx, m.values, b, rtol=1e-10, inner_rtol=1e-3,
+                              adaptive=False)
+    assert info["converged"]
+    assert 2 <= info["outer_iterations"] <= 5
+    assert info["rel_residual"] <= 1e-10
+
+
 @pytest.mark.parametrize("adaptive", [False, True])
 def test_mixed_ir_reaches_fp64_residual(oracle, adaptive):
     m, rng = meshgen.kuhn_tet_matrix(6, seed=0, dirichlet=True)
