@@ -50,37 +50,41 @@ _lib = None
 def lib():
     global _lib
     if _lib is None:
-        _lib = ctypes.CDLL(build())
-        L = _lib
-        L.oracle_csr_spmv.argtypes = [_i32, _i32p, _i32p, _f64p, _f64p, _f64p, _int]
-        L.oracle_csr_spmv.restype = None
-        L.oracle_csr_spmv_f32.argtypes = [_i32, _i32p, _i32p, _f32p, _f32p, _f32p, _int]
-        L.oracle_csr_spmv_f32.restype = None
-        L.oracle_csr_spmv_axpby.argtypes = [_i32, _i32p, _i32p, _f64p, _f64, _f64p, _f64, _f64p]
-        L.oracle_csr_spmv_axpby.restype = None
-        L.oracle_spmm.argtypes = [_i32, _i32p, _i32p, _f64p, _i32, _f64p, _f64p, _int]
-        L.oracle_spmm.restype = None
-        L.oracle_spmm_f32.argtypes = [_i32, _i32p, _i32p, _f32p, _i32, _f32p, _f32p, _int]
-        L.oracle_spmm_f32.restype = None
-        L.oracle_cm_order.argtypes = [_i32, _i32p, _i32p, _int, _int, _i32p]
-        L.oracle_cm_order.restype = _int
-        L.oracle_sigma_sort.argtypes = [_i32, _i32p, ctypes.c_void_p, _i32, _i32p]
-        L.oracle_sigma_sort.restype = _int
-        L.oracle_permute_csr.argtypes = [_i32, _i32p, _i32p, _f64p, _i32p, _i32p, _i32p, _f64p]
-        L.oracle_permute_csr.restype = _int
-        L.oracle_sell_slice_ptr.argtypes = [_i32, _i32p, _i32, _i64p]
-        L.oracle_sell_slice_ptr.restype = ctypes.c_int64
-        L.oracle_sell_fill.argtypes = [_i32, _i32p, _i32p, _f64p, _i32, _i64p, _i32p, _f64p]
-        L.oracle_sell_fill.restype = None
-        L.oracle_window_meta.argtypes = [_i32, _i32, _i64p, _i32p, _i32p, _i32p]
-        L.oracle_window_meta.restype = None
-        L.oracle_jacobi_pcg.argtypes = [_i32, _i32p, _i32p, _f64p, _f64p, _f64p, _f64, _i32,
-                                        _i32, _PI32, _PF64, _PF64]
-        L.oracle_jacobi_pcg.restype = _int
-        L.oracle_mixed_ir.argtypes = [_i32, _i32p, _i32p, _f64p, _f64p, _f64p, _f64, _f64, _i32,
-                                      _i32, _int, _PI32, _PI32, _PF64]
-        L.oracle_mixed_ir.restype = _int
+        _lib = _configure(ctypes.CDLL(build()))
     return _lib
+
+
+def _configure(L):
+    """Argument and result types of the oracle's C functions on a loaded library."""
+    L.oracle_csr_spmv.argtypes = [_i32, _i32p, _i32p, _f64p, _f64p, _f64p, _int]
+    L.oracle_csr_spmv.restype = None
+    L.oracle_csr_spmv_f32.argtypes = [_i32, _i32p, _i32p, _f32p, _f32p, _f32p, _int]
+    L.oracle_csr_spmv_f32.restype = None
+    L.oracle_csr_spmv_axpby.argtypes = [_i32, _i32p, _i32p, _f64p, _f64, _f64p, _f64, _f64p]
+    L.oracle_csr_spmv_axpby.restype = None
+    L.oracle_spmm.argtypes = [_i32, _i32p, _i32p, _f64p, _i32, _f64p, _f64p, _int]
+    L.oracle_spmm.restype = None
+    L.oracle_spmm_f32.argtypes = [_i32, _i32p, _i32p, _f32p, _i32, _f32p, _f32p, _int]
+    L.oracle_spmm_f32.restype = None
+    L.oracle_cm_order.argtypes = [_i32, _i32p, _i32p, _int, _int, _i32p]
+    L.oracle_cm_order.restype = _int
+    L.oracle_sigma_sort.argtypes = [_i32, _i32p, ctypes.c_void_p, _i32, _i32p]
+    L.oracle_sigma_sort.restype = _int
+    L.oracle_permute_csr.argtypes = [_i32, _i32p, _i32p, _f64p, _i32p, _i32p, _i32p, _f64p]
+    L.oracle_permute_csr.restype = _int
+    L.oracle_sell_slice_ptr.argtypes = [_i32, _i32p, _i32, _i64p]
+    L.oracle_sell_slice_ptr.restype = ctypes.c_int64
+    L.oracle_sell_fill.argtypes = [_i32, _i32p, _i32p, _f64p, _i32, _i64p, _i32p, _f64p]
+    L.oracle_sell_fill.restype = None
+    L.oracle_window_meta.argtypes = [_i32, _i32, _i64p, _i32p, _i32p, _i32p]
+    L.oracle_window_meta.restype = None
+    L.oracle_jacobi_pcg.argtypes = [_i32, _i32p, _i32p, _f64p, _f64p, _f64p, _f64, _i32,
+                                    _i32, _PI32, _PF64, _PF64]
+    L.oracle_jacobi_pcg.restype = _int
+    L.oracle_mixed_ir.argtypes = [_i32, _i32p, _i32p, _f64p, _f64p, _f64p, _f64, _f64, _i32,
+                                  _i32, _int, _PI32, _PI32, _PF64]
+    L.oracle_mixed_ir.restype = _int
+    return L
 
 
 def _csr(row_ptr, col_idx):
