@@ -159,6 +159,33 @@ def test_mixed_generator_reduces_to_kuhn_and_keeps_invariants():
     assert np.diff(md.row_ptr).max() <= 13
 
 
+def test_dirichlet_spectrum_matches_continuum_and_neumann_is_semidefinite():
+    """Smallest Lanczos Ritz value of the 20^3 Dirichlet matrix (48,000 cells) is positive and
+    approximates the continuum one: the FV matrix with face weights area/distance behaves like
+    V_cell * (-Laplacian), whose smallest Dirichlet eigenvalue on the unit cube is 3 pi^2, with
+    V_cell = h^3 / 6 for the six Kuhn tets of a hexahedron (discretisation error O(h^2)).
+    The Neumann matrix is negative semidefinite with the constants as its null space."""
+    sla = pytest.importorskip("scipy.sparse.linalg")
+    sp = pytest.importorskip("scipy.sparse")
+    n = 20
+    md, _ = meshgen.kuhn_tet_matrix(n, seed=0, dirichlet=True)
+    A = sp.csr_matrix((md.values, md.col_idx, md.row_ptr), shape=(md.n, md.n))
+    lam = sla.eigsh(A, k=1, which="SA", return_eigenvectors=False, tol=1e-8, maxiter=20000)[0]
+    assert lam > 0.0
+    assert abs(lam / (3.0 * math.pi ** 2 / (6.0 * n ** 3)) - 1.0) < 0.05
+    mn, _ = meshgen.kuhn_tet_matrix(8, seed=0, dirichlet=False)
+    w = np.linalg.eigvalsh(mn.to_dense())
+    scale = np.abs(w).max()
+    assert w[-1] <= 1e-13 * scale and abs(w[-1]) <= 1e-13 * scale  # one zero eigenvalue
+    assert w[-2] < -1e-6 * scale  # connected mesh: the zero is simple
+
+
+def test_generator_rejects_inverted_tets():
+    """The orientation check is live: jitter of half a cell width inverts some tetrahedra."""
+    with pytest.raises(ValueError, match="inverted"):
+        meshgen.kuhn_tet_matrix(5, jitter=0.5, seed=0)
+
+
 def test_generator_deterministic():
     a, _ = meshgen.kuhn_tet_matrix(4, seed=11, dirichlet=True)
     b, _ = meshgen.kuhn_tet_matrix(4, seed=11, dirichlet=True)
