@@ -34,7 +34,7 @@ sys.path.insert(0, ROOT)
 METRIC = "SpMV effective GB/s (% HBM peak) FP64 vs mixed; served CG solves/s, p99"
 WORKLOAD = "kuhn-tet 100^3 FV Laplacian, Dirichlet, 6,000,000 rows, 29,880,000 nnz, RCM order"
 FLUSH_BYTES = 512 << 20
-VARIANTS = {0: "auto", 1: "spmv_csr", 2: "spmv_sell", 3: "spmv_sell_window"}  # 256 MB written + 256 MB read between timed steps
+VARIANTS = {0: "auto", 1: "spmv_csr", 2: "spmv_sell", 3: "spmv_sell_window", 4: "spmv_sell_bulk"}  # 256 MB written + 256 MB read between timed steps
 
 
 def spmv_bytes(n, nnz, f32=False):
@@ -312,7 +312,8 @@ def run_gpu(args):
     stream = torch.cuda.Stream(device=dev)
     t_create = time.perf_counter()
     variant = {"auto": capi.SPMV_VARIANT_AUTO, "sell": capi.SPMV_VARIANT_SELL,
-               "csr": capi.SPMV_VARIANT_CSR, "window": capi.SPMV_VARIANT_SELL_WINDOW}[args.variant]
+               "csr": capi.SPMV_VARIANT_CSR, "window": capi.SPMV_VARIANT_SELL_WINDOW,
+               "bulk": capi.SPMV_VARIANT_SELL_BULK}[args.variant]
     A = capi.Matrix(n, m.row_ptr, m.col_idx, m.values, stream=stream,
                     reorder=capi.SPMV_REORDER_RCM, precision=capi.SPMV_PREC_DUAL,
                     slice_height=args.slice_height, autotune=int(args.autotune),
@@ -884,7 +885,7 @@ def main():
                     help="1: the headline handle picks S, CTA size and variant by timing")
     ap.add_argument("--quick", action="store_true", help="headline only, no secondary results")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--variant", default="auto", choices=["auto", "sell", "csr", "window"],
+    ap.add_argument("--variant", default="auto", choices=["auto", "sell", "csr", "window", "bulk"],
                     help="kernel variant of the headline handle (auto: default / autotuned)")
     ap.add_argument("--index-bits", type=int, default=0, choices=[0, 16, 32])
     ap.add_argument("--f32", action="store_true",

@@ -64,6 +64,10 @@ typedef enum {
 #define SPMV_VARIANT_CSR 1         /* thread per CSR row, x gathered from global memory (Sec. 4.3) */
 #define SPMV_VARIANT_SELL 2        /* sliced ELLPACK, A streamed, x kept resident in L2        */
 #define SPMV_VARIANT_SELL_WINDOW 3 /* sliced ELLPACK, x staged per CTA in a shared-memory window (Sec. 5.1) */
+#define SPMV_VARIANT_SELL_BULK 4   /* sliced ELLPACK, x kept resident in L2, the matrix streamed
+                                    * into a ring of shared-memory stages by bulk asynchronous
+                                    * copies (one CTA per SM; falls back to SELL when a slice
+                                    * does not fit a stage).  Same summation order as SELL. */
 
 typedef struct {
     int slice_height;    /* S, rows per slice: 32, 64, 128 or 256 (0 = default 64)            */
@@ -264,6 +268,27 @@ spmv_status_t spmv_verify(spmv_matrix_t A, int *violations, void *stream);
  * stored entry.
  */
 spmv_status_t spmv_diag_checks(spmv_matrix_t A, int *planted, int *detected, void *stream);
+
+/*
+ * spmv_device_status -- sync (waits for the stream).  Returns SPMV_ERR_TIMEOUT when a kernel
+ * launched on the handle gave up one of its bounded waits since the handle was created or since
+ * the last call (the staged product of SPMV_VARIANT_SELL_BULK waits on shared-memory barriers
+ * for at most one second; a product that gave up left part of y unwritten), else SPMV_OK.  The
+ * record is cleared.  INVALID_ARG for a NULL handle.
+ */
+spmv_status_t spmv_device_status(spmv_matrix_t A, void *stream);
+
+/*
+ * spmv_diag_bulk_timeout -- sync.  Self-test of the staged product's bounded waits: runs one
+ * SPMV_VARIANT_SELL_BULK product of the handle (x = 0 in a scratch buffer; FP64 values when the
+ * handle has them, else FP32) in which the first warp never copies its first slice, so that its
+ * wait runs out after one second; the warp records the fact, waits for its other copies and
+ * exits, while the rest of the product completes.  Returns SPMV_ERR_TIMEOUT when the expired
+ * wait was recorded (the expected outcome; the record is cleared and the handle stays usable),
+ * SPMV_ERR_CUDA when it was not, SPMV_ERR_UNSUPPORTED when the handle's slices do not fit the
+ * staged product, INVALID_ARG for a NULL or empty handle.
+ */
+spmv_status_t spmv_diag_bulk_timeout(spmv_matrix_t A, void *stream);
 
 /* ------------------------------ conjugate gradients ------------------------------------ */
 typedef struct {

@@ -31,6 +31,7 @@ SPMV_ERR_CANCELLED = 10
 SPMV_REORDER_NONE, SPMV_REORDER_RCM, SPMV_REORDER_CM = 0, 1, 2
 SPMV_PREC_FP64, SPMV_PREC_FP32, SPMV_PREC_DUAL = 0, 1, 2
 SPMV_VARIANT_AUTO, SPMV_VARIANT_CSR, SPMV_VARIANT_SELL, SPMV_VARIANT_SELL_WINDOW = 0, 1, 2, 3
+SPMV_VARIANT_SELL_BULK = 4
 
 
 class spmv_options_t(ctypes.Structure):
@@ -123,6 +124,8 @@ _SIGS = {
     "spmv_apply_chain_f32": [_P, _P, _P, _P, _P],
     "spmv_apply_host_async": [_P, _P, _P, _P],
     "spmv_verify": [_P, ctypes.POINTER(_int), _P],
+    "spmv_device_status": [_P, _P],
+    "spmv_diag_bulk_timeout": [_P, _P],
     "spmv_diag_checks": [_P, ctypes.POINTER(_int), ctypes.POINTER(_int), _P],
 }
 
@@ -238,6 +241,21 @@ def spmv_verify(h, stream=None):
     if st not in (SPMV_OK, SPMV_ERR_INVALID_CSR):
         raise SpmvError(st, "spmv_verify")
     return v.value
+
+
+def spmv_device_status(h, stream=None):
+    """SPMV_ERR_TIMEOUT when a kernel on the handle gave up a bounded wait since the last call,
+    else SPMV_OK (the record is cleared)."""
+    st = load().spmv_device_status(h, _stream(stream))
+    if st not in (SPMV_OK, SPMV_ERR_TIMEOUT):
+        raise SpmvError(st, "spmv_device_status")
+    return st
+
+
+def spmv_diag_bulk_timeout(h, stream=None):
+    """Self-test of the staged product's bounded wait; returns the status (SPMV_ERR_TIMEOUT is
+    the expected outcome)."""
+    return load().spmv_diag_bulk_timeout(h, _stream(stream))
 
 
 def spmv_diag_checks(h, stream=None):

@@ -3,8 +3,8 @@
 // warm-up launches).  Each slice height needs its own sliced-ELLPACK arrays, so the arrays are
 // rebuilt per candidate and finally for the winner.  Candidates: S in {32, 64, 128, 256}
 // (S = 512 of the FPGA design is a pipelining depth, Sec. 6.1, and has no GPU meaning),
-// CTA sizes {128, 256, 512}, the shared-memory window variant, and the naive CSR kernel
-// (FP64 handles).
+// CTA sizes {128, 256, 512}, the matrix staged by bulk copies, the shared-memory window
+// variant, and the naive CSR kernel (FP64 handles).
 #include <algorithm>
 #include <vector>
 
@@ -73,6 +73,18 @@ spmv_status_t autotune_matrix(spmv_matrix_t A, cudaStream_t st) {
             }
         }
         if (s != SPMV_OK) break;
+        if (user_variant == SPMV_VARIANT_AUTO || user_variant == SPMV_VARIANT_SELL_BULK) {
+            // matrix staged through shared memory by bulk copies (one CTA per SM)
+            A->variant = SPMV_VARIANT_SELL_BULK;
+            float ms;
+            s = time_launch(A, x, y, st, e0, e1, &ms);
+            if (s != SPMV_OK) break;
+            if (ms < best) {
+                best = ms;
+                best_S = S;
+                best_variant = SPMV_VARIANT_SELL_BULK;
+            }
+        }
         if (user_variant == SPMV_VARIANT_AUTO || user_variant == SPMV_VARIANT_SELL_WINDOW) {
             // shared-memory window of x (one 1024-thread CTA per SM)
             A->variant = SPMV_VARIANT_SELL_WINDOW;

@@ -50,7 +50,7 @@ static spmv_status_t normalize_options(const spmv_options_t *in, spmv_options_t 
     const int S = o->slice_height;
     if (S != 32 && S != 64 && S != 128 && S != 256) return SPMV_ERR_INVALID_ARG;
     if (o->block < 64 || o->block > 1024 || (o->block % 32) != 0) return SPMV_ERR_INVALID_ARG;
-    if (o->variant < SPMV_VARIANT_AUTO || o->variant > SPMV_VARIANT_SELL_WINDOW)
+    if (o->variant < SPMV_VARIANT_AUTO || o->variant > SPMV_VARIANT_SELL_BULK)
         return SPMV_ERR_INVALID_ARG;
     if (o->reorder < SPMV_REORDER_NONE || o->reorder > SPMV_REORDER_CM) return SPMV_ERR_INVALID_ARG;
     if (o->precision < SPMV_PREC_FP64 || o->precision > SPMV_PREC_DUAL) return SPMV_ERR_INVALID_ARG;
@@ -202,6 +202,26 @@ spmv_status_t spmv_verify(spmv_matrix_t A, int *violations, void *stream) {
     GB_TRY(verify_matrix(A, st, &flags));
     if (violations) *violations = flags;
     return flags ? SPMV_ERR_INVALID_CSR : SPMV_OK;
+}
+
+spmv_status_t spmv_device_status(spmv_matrix_t A, void *stream) {
+    if (!A) return SPMV_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!A->dev_status.p) return SPMV_OK;
+    int v = 0;
+    GB_CUDA(cudaMemcpyAsync(&v, A->dev_status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GB_CUDA(cudaMemsetAsync(A->dev_status.p, 0, sizeof(int), st));
+    GB_CUDA(cudaStreamSynchronize(st));
+    return v ? SPMV_ERR_TIMEOUT : SPMV_OK;
+}
+
+spmv_status_t spmv_diag_bulk_timeout(spmv_matrix_t A, void *stream) {
+    if (!A || A->n == 0 || A->sell_entries == 0) return SPMV_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    AllocStream alloc_scope(st);
+    int recorded = 0;
+    GB_TRY(bulk_diag_timeout(A, st, &recorded));
+    return (recorded & 1) ? SPMV_ERR_TIMEOUT : SPMV_ERR_CUDA;
 }
 
 spmv_status_t spmv_diag_checks(spmv_matrix_t A, int *planted, int *detected, void *stream) {
@@ -391,6 +411,8 @@ void release_matrix(spmv_matrix_t A) {
     A->sell_val32.release(t);
     A->col_start.release(t);
     A->col_end.release(t);
+    A->bulk_part.release(t);
+    A->dev_status.release(t);
     delete A;
 }
 

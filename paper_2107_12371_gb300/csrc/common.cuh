@@ -148,6 +148,7 @@ struct spmv_matrix_s {
     int32_t bandwidth = 0;
     int32_t max_span = 0;
     int32_t n_slices = 0;
+    int32_t max_width = 0;  // widest slice: its stored entries per row
     int64_t sell_entries = 0;
     size_t bytes = 0;  // device bytes owned
 
@@ -163,6 +164,9 @@ struct spmv_matrix_s {
     gb::DevBuf<float> sell_val32;
     gb::DevBuf<int32_t> col_start;  // per-slice x range (Sec. 5.1)
     gb::DevBuf<int32_t> col_end;
+    int bulk_G = 0;                  // CTAs of the staged product (SPMV_VARIANT_SELL_BULK)
+    gb::DevBuf<int32_t> bulk_part;   // CTA b takes slices [bulk_part[b], bulk_part[b + 1])
+    gb::DevBuf<int> dev_status;      // bit 0: a staged product gave up a bounded wait
     gb::CgWork cg;
 
     // spmv_apply_host(_async): two staging sets used in turn, each with device copies of x and
@@ -206,6 +210,15 @@ int window_capacity_words(int elem_bytes);
 spmv_status_t launch_window64(spmv_matrix_t A, const double *x, double *y, cudaStream_t st);
 spmv_status_t launch_window32(spmv_matrix_t A, const float *x, float *y, cudaStream_t st);
 spmv_status_t choose_variant(spmv_matrix_t A, cudaStream_t st);
+
+// staged product (bulk.cu): per-CTA slice runs of a handle, and the launches (*launched =
+// false when the handle's slices do not fit the shared-memory stages: nothing was enqueued)
+spmv_status_t bulk_partition(spmv_matrix_t A, cudaStream_t st);
+spmv_status_t launch_bulk64(spmv_matrix_t A, const double *x, double *y, cudaStream_t st,
+                            bool *launched);
+spmv_status_t launch_bulk32(spmv_matrix_t A, const float *x, float *y, cudaStream_t st,
+                            bool *launched);
+spmv_status_t bulk_diag_timeout(spmv_matrix_t A, cudaStream_t st, int *recorded);
 
 // device scan utilities (scan.cu): exclusive prefix sum of n int64 values in place; the
 // total is written to out[n] (the array holds n + 1 entries).

@@ -481,7 +481,7 @@ __global__ void sell_scatter(int32_t n, int32_t S, int64_t n_pad, const int32_t 
 }
 
 __global__ void window_meta(int32_t n_slices, int32_t S, const int64_t *sp, const int32_t *scol,
-                            int32_t *cs, int32_t *ce, int *max_span) {
+                            int32_t *cs, int32_t *ce, int *max_span_width) {
     const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (s >= n_slices) return;
@@ -506,10 +506,10 @@ __global__ void window_meta(int32_t n_slices, int32_t S, const int64_t *sp, cons
         } else {
             cs[s] = lo;
             ce[s] = hi + 1;
-            atomicMax(max_span, hi + 1 - lo);
+            atomicMax(max_span_width, hi + 1 - lo);
         }
+        atomicMax(max_span_width + 1, (int)((sp[s + 1] - sp[s]) / S));
     }
-    (void)S;
 }
 
 // 16-bit columns relative to the slice's first column (Sec. 5.1); padding -> 0xFFFF
@@ -565,19 +565,27 @@ spmv_status_t build_sell(spmv_matrix_t A, int S, cudaStream_t st) {
     GB_LAUNCHED();
     GB_TRY(A->col_start.alloc((size_t)n_slices, tally));
     GB_TRY(A->col_end.alloc((size_t)n_slices, tally));
-    int *d_span = nullptr;
-    GB_CUDA(gb_malloc_async((void **)&d_span, sizeof(int), st));
-    cudaMemsetAsync(d_span, 0, sizeof(int), st);
+    int *d_span = nullptr;  // max span, max width
+    GB_CUDA(gb_malloc_async((void **)&d_span, 2 * sizeof(int), st));
+    cudaMemsetAsync(d_span, 0, 2 * sizeof(int), st);
     window_meta<<<blocks_for((int64_t)n_slices * 32), kT, 0, st>>>(
         n_slices, S, A->slice_ptr.p, A->sell_col.p, A->col_start.p, A->col_end.p, d_span);
     spmv_status_t s = cuda_status(cudaGetLastError());
-    int span = 0;
+    int span_width[2] = {0, 0};
     if (s == SPMV_OK)
-        s = cuda_status(cudaMemcpyAsync(&span, d_span, sizeof(int), cudaMemcpyDeviceToHost, st));
+        s = cuda_status(cudaMemcpyAsync(span_width, d_span, 2 * sizeof(int),
+                                        cudaMemcpyDeviceToHost, st));
     cudaFreeAsync(d_span, st);
     if (s == SPMV_OK) s = cuda_status(cudaStreamSynchronize(st));
     if (s != SPMV_OK) return s;
+    const int span = span_width[0];
     A->max_span = span;
+    A->max_width = span_width[1];
+    GB_TRY(bulk_partition(A, st));
+    if (!A->dev_status.p) {
+        GB_TRY(A->dev_status.alloc(1, tally));
+        GB_CUDA(cudaMemsetAsync(A->dev_status.p, 0, sizeof(int), st));
+    }
     // 16-bit relative columns when every slice spans fewer than 65,535 columns
     const int want = A->opt.index_bits;
     A->sell_col16.release(tally);

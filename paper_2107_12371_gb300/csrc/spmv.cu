@@ -175,6 +175,11 @@ spmv_status_t launch_sell(spmv_matrix_t A, const T *val, const T *x, T *y, T alp
 spmv_status_t launch_spmv64(spmv_matrix_t A, const double *x, double *y, cudaStream_t st) {
     if (A->variant == SPMV_VARIANT_CSR) return launch_spmv_csr64(A, x, y, st);
     if (A->variant == SPMV_VARIANT_SELL_WINDOW) return launch_window64(A, x, y, st);
+    if (A->variant == SPMV_VARIANT_SELL_BULK) {
+        bool launched = false;
+        GB_TRY(launch_bulk64(A, x, y, st, &launched));
+        if (launched) return SPMV_OK;
+    }
     return launch_sell<double>(A, A->sell_val.p, x, y, 1.0, 0.0, st);
 }
 
@@ -190,6 +195,11 @@ spmv_status_t launch_axpby32(spmv_matrix_t A, float alpha, const float *x, float
 
 spmv_status_t launch_spmv32(spmv_matrix_t A, const float *x, float *y, cudaStream_t st) {
     if (A->variant == SPMV_VARIANT_SELL_WINDOW) return launch_window32(A, x, y, st);
+    if (A->variant == SPMV_VARIANT_SELL_BULK) {
+        bool launched = false;
+        GB_TRY(launch_bulk32(A, x, y, st, &launched));
+        if (launched) return SPMV_OK;
+    }
     return launch_sell<float>(A, A->sell_val32.p, x, y, 1.0f, 0.0f, st);
 }
 

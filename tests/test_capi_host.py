@@ -107,4 +107,6 @@ def test_entry_points_reject_null_handles(lib):
     assert L.spmv_apply_chain_f32(None, None, None, None, None) == capi.SPMV_ERR_INVALID_ARG
     assert L.spmv_verify(None, None, None) == capi.SPMV_ERR_INVALID_ARG
     assert L.spmv_diag_checks(None, None, None, None) == capi.SPMV_ERR_INVALID_ARG
+    assert L.spmv_device_status(None, None) == capi.SPMV_ERR_INVALID_ARG
+    assert L.spmv_diag_bulk_timeout(None, None) == capi.SPMV_ERR_INVALID_ARG
     assert L.spmv_server_destroy(None) == capi.SPMV_OK

@@ -127,7 +127,8 @@ def test_autotuned_handle_parity(oracle, precision):
                     reorder=capi.SPMV_REORDER_RCM)
     info = A.info()
     assert info["slice_height"] in (32, 64, 128, 256) and info["block"] in (128, 256, 512)
-    assert info["variant"] in (capi.SPMV_VARIANT_SELL, capi.SPMV_VARIANT_CSR)
+    assert info["variant"] in (capi.SPMV_VARIANT_SELL, capi.SPMV_VARIANT_CSR,
+                               capi.SPMV_VARIANT_SELL_BULK, capi.SPMV_VARIANT_SELL_WINDOW)
     rp, ci, v = capi.spmv_export_csr(A.handle, m.n, m.nnz)
     mi = meshgen.CsrMatrix(m.n, rp, ci, v)
     xi = x[A.permutation()]
@@ -168,6 +169,62 @@ def test_window_variant_wide_and_ragged(oracle):
     x = np.random.default_rng(12).uniform(-1, 1, m.n)
     A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values, variant=capi.SPMV_VARIANT_SELL_WINDOW)
     check_fp64(m, x, gpu_spmv(A, x), oracle)
+
+
+@pytest.mark.parametrize("reorder", [capi.SPMV_REORDER_NONE, capi.SPMV_REORDER_RCM])
+@pytest.mark.parametrize("bits", [16, 32])
+@pytest.mark.parametrize("S", [32, 64, 128, 256])
+def test_bulk_variant_parity(oracle, S, bits, reorder):
+    """Matrix staged in shared memory by bulk asynchronous copies: FP64 and FP32 products
+    bit-identical to the oracle (same per-row order as the register-streaming kernel), and no
+    bounded wait gave up."""
+    m, x = workloads.c1()
+    A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values, slice_height=S, index_bits=bits,
+                    variant=capi.SPMV_VARIANT_SELL_BULK, precision=capi.SPMV_PREC_DUAL,
+                    reorder=reorder)
+    info = A.info()
+    assert info["variant"] == capi.SPMV_VARIANT_SELL_BULK
+    rp, ci, v = capi.spmv_export_csr(A.handle, m.n, m.nnz)
+    mi = meshgen.CsrMatrix(m.n, rp, ci, v)
+    xi = x[A.permutation()]
+    check_fp64(mi, xi, gpu_spmv(A, xi), oracle)
+    x32 = xi.astype(np.float32)
+    ref = oracle.spmv_f32(rp, ci, v.astype(np.float32), x32, use_fma=True)
+    assert np.array_equal(gpu_spmv(A, x32, f32=True), ref)
+    assert capi.spmv_device_status(A.handle) == capi.SPMV_OK
+
+
+@pytest.mark.parametrize("n,max_len,S", [(20000, 12, 64), (20000, 60, 32), (3001, 40, 256),
+                                         (37, 9, 64), (1, 1, 32)])
+def test_bulk_variant_ragged_wide_and_tiny(oracle, n, max_len, S):
+    """Ragged rows (empty rows, a ragged last slice, slices of very different widths), slices
+    too wide for a stage (the handle falls back to the register-streaming kernel) and matrices
+    smaller than one slice or than one CTA per SM."""
+    m = ragged_matrix(n, 11 + n, max_len=max_len)
+    x = np.random.default_rng(12).uniform(-1, 1, m.n)
+    A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values, slice_height=S,
+                    variant=capi.SPMV_VARIANT_SELL_BULK, precision=capi.SPMV_PREC_DUAL)
+    check_fp64(m, x, gpu_spmv(A, x), oracle)
+    x32 = x.astype(np.float32)
+    ref = oracle.spmv_f32(m.row_ptr, m.col_idx, m.values.astype(np.float32), x32, use_fma=True)
+    assert np.array_equal(gpu_spmv(A, x32, f32=True), ref)
+    assert capi.spmv_device_status(A.handle) == capi.SPMV_OK
+
+
+def test_bulk_wait_runs_out_with_a_status(oracle):
+    """Failure detection without a GPU fault: in a staged product whose first warp never copies
+    its first slice, that warp's bounded wait runs out, is recorded and reported, the rest of the
+    product completes, and the handle keeps working."""
+    import time
+    m, x = workloads.c1()
+    A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values, variant=capi.SPMV_VARIANT_SELL_BULK,
+                    precision=capi.SPMV_PREC_DUAL)
+    t0 = time.time()
+    assert capi.spmv_diag_bulk_timeout(A.handle) == capi.SPMV_ERR_TIMEOUT
+    assert time.time() - t0 < 10.0
+    assert capi.spmv_device_status(A.handle) == capi.SPMV_OK  # the record was cleared
+    check_fp64(m, x, gpu_spmv(A, x), oracle)
+    assert capi.spmv_device_status(A.handle) == capi.SPMV_OK
 
 
 @pytest.mark.parametrize("alpha,beta", [(1.0, 0.0), (2.5, -0.75), (-1.0, 1.0)])
@@ -576,13 +633,15 @@ def test_checks_detect_planted_faults(case):
 # ---------------------------------------------------------------------------------------
 # full size: the 6M-cell Dirichlet mesh in the benchmark's launch configuration
 # ---------------------------------------------------------------------------------------
-@pytest.mark.parametrize("reorder,bits", [(capi.SPMV_REORDER_NONE, 0),
-                                          (capi.SPMV_REORDER_RCM, 16),
-                                          (capi.SPMV_REORDER_RCM, 32)])
-def test_c2_full_size_parity(oracle, reorder, bits):
+@pytest.mark.parametrize("reorder,bits,variant", [
+    (capi.SPMV_REORDER_NONE, 0, capi.SPMV_VARIANT_AUTO),
+    (capi.SPMV_REORDER_RCM, 16, capi.SPMV_VARIANT_AUTO),
+    (capi.SPMV_REORDER_RCM, 32, capi.SPMV_VARIANT_AUTO),
+    (capi.SPMV_REORDER_RCM, 16, capi.SPMV_VARIANT_SELL_BULK)])
+def test_c2_full_size_parity(oracle, reorder, bits, variant):
     m, x = workloads.c2()
     A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values, reorder=reorder,
-                    precision=capi.SPMV_PREC_DUAL, index_bits=bits)
+                    precision=capi.SPMV_PREC_DUAL, index_bits=bits, variant=variant)
     if bits:
         assert A.info()["index_bits"] == bits
     xd = dev(x)
@@ -605,3 +664,4 @@ def test_c2_full_size_parity(oracle, reorder, bits):
     y32 = gpu_spmv(A, x32, f32=True)
     ref32 = oracle.spmv_f32(rp, ci, v.astype(np.float32), x32, use_fma=True)
     assert np.array_equal(y32, ref32)
+    assert capi.spmv_device_status(A.handle) == capi.SPMV_OK
