@@ -501,6 +501,26 @@ def test_spmm_16_byte_aligned_blocks(oracle, k, dtype):
     assert np.array_equal(Yd.cpu().numpy(), ref)
 
 
+@pytest.mark.parametrize("k,dtype", [(8, np.float64), (32, np.float64), (32, np.float32)])
+def test_spmm_full_size_parity(oracle, k, dtype):
+    """The SpMM workload of the benchmark at full size -- mixed hexahedron / prism /
+    tetrahedron mesh of 87^3 hexahedra (about 1.98M cells), RCM and sigma = 1024 sorting, 16-bit
+    columns, the 256-bit kernel -- bit-identical to the oracle on every entry."""
+    m, X = workloads.mixed(87, seed=1, k=32)
+    A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values, reorder=capi.SPMV_REORDER_RCM,
+                    precision=capi.SPMV_PREC_DUAL, sigma=1024)
+    assert A.info()["index_bits"] == 16
+    rp, ci, v = capi.spmv_export_csr(A.handle, m.n, m.nnz)
+    Xi = np.ascontiguousarray(X[A.permutation(), :k]).astype(dtype)
+    Xd = dev(Xi)
+    Yd = torch.empty_like(Xd)
+    assert Xd.data_ptr() % 32 == 0 and Yd.data_ptr() % 32 == 0
+    A.apply_multi(Xd, Yd)
+    torch.cuda.synchronize()
+    ref = oracle.spmm(rp, ci, v.astype(dtype), Xi, use_fma=True)
+    assert np.array_equal(Yd.cpu().numpy(), ref)
+
+
 # ---------------------------------------------------------------------------------------
 # products with host vectors (copies pipelined with the product inside the call)
 # ---------------------------------------------------------------------------------------
