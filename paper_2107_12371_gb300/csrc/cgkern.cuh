@@ -17,12 +17,16 @@ int cg_grid(int32_t n);
 // The product phase q = A p, p.q runs on a grid of its own: the sweeps' grid (at most
 // kCgCtasPerSm CTAs per SM, 64 registers) leaves the latency-bound gathers without enough
 // warps, so the product takes up to pq_min_ctas CTAs per SM (40 registers where a lane
-// holds at most 16 bytes of values per entry) and at most one slice-lane per thread.  The
+// holds at most 16 bytes of values per entry) and at most one slice-lane per thread.  An FP32
+// lane of at most 16 bytes instead keeps pq_unroll = 5 entries in flight (a whole row of the
+// tetrahedral meshes) at four CTAs per SM and 64 registers: measured 4.7 % faster for the
+// whole refinement solve of the 6M-row mesh than two entries at six CTAs per SM.  The
 // persistent kernel runs the same grid as virtual CTAs, so both paths stay bit-identical.
-constexpr int pq_min_ctas(int value_bytes) {
-    return value_bytes >= 64 ? 3 : value_bytes >= 32 ? 4 : 6;
+constexpr int pq_min_ctas(int value_bytes, bool f32) {
+    return f32 && value_bytes <= 16 ? 4 : value_bytes >= 64 ? 3 : value_bytes >= 32 ? 4 : 6;
 }
-int cg_pq_grid(int32_t n_slices, int L, int value_bytes);
+constexpr int pq_unroll(int value_bytes, bool f32) { return f32 && value_bytes <= 16 ? 5 : 2; }
+int cg_pq_grid(int32_t n_slices, int L, int value_bytes, bool f32);
 
 // Hint: bring the line holding p into L1 without waiting for it (a later load of it hits).
 __device__ __forceinline__ void prefetch_l1(const void *p) {
@@ -112,7 +116,7 @@ __device__ bool grid_sum_last(double (&v)[NV], double *part, unsigned *ticket, d
 // y-rows (R of them) of lane `lane` in slice `slice`: sum over the slice's columns in order,
 // fused multiply-add from +0.0, padding skipped (the same order as spmv_sell).  COHERENT
 // selects coherent gathers of x, for kernels in which other CTAs rewrite x between barriers.
-template <typename T, int R, int L, bool COHERENT = false, typename ColT>
+template <typename T, int R, int L, bool COHERENT = false, int UU = 2, typename ColT>
 __device__ __forceinline__ void slice_rows(int64_t slice, int lane, const int64_t *sp,
                                            const ColT &cols, const T *val, const T *x,
                                            uint64_t pol, T (&acc)[R]) {
@@ -125,22 +129,23 @@ __device__ __forceinline__ void slice_rows(int64_t slice, int lane, const int64_
 #pragma unroll
     for (int i = 0; i < R; ++i) acc[i] = T(0);
     int t = 0;
-    for (; t + 2 <= w; t += 2) {
-        T v[2][R];
-        int32_t c[2][R];
-        ld_stream(vp + (int64_t)t * S, pol, v[0]);
-        cols.template load<R>(cat + (int64_t)t * S, slice, pol, cbase, c[0]);
-        ld_stream(vp + (int64_t)(t + 1) * S, pol, v[1]);
-        cols.template load<R>(cat + (int64_t)(t + 1) * S, slice, pol, cbase, c[1]);
-        T xv[2][R];
+    for (; t + UU <= w; t += UU) {
+        T v[UU][R];
+        int32_t c[UU][R];
 #pragma unroll
-        for (int u = 0; u < 2; ++u)
+        for (int u = 0; u < UU; ++u) {
+            ld_stream(vp + (int64_t)(t + u) * S, pol, v[u]);
+            cols.template load<R>(cat + (int64_t)(t + u) * S, slice, pol, cbase, c[u]);
+        }
+        T xv[UU][R];
+#pragma unroll
+        for (int u = 0; u < UU; ++u)
 #pragma unroll
             for (int i = 0; i < R; ++i)
                 xv[u][i] = c[u][i] >= 0 ? (COHERENT ? ld_x_coherent(x + c[u][i]) : ld_x(x + c[u][i]))
                                         : T(0);
 #pragma unroll
-        for (int u = 0; u < 2; ++u)
+        for (int u = 0; u < UU; ++u)
 #pragma unroll
             for (int i = 0; i < R; ++i)
                 if (c[u][i] >= 0) acc[i] = fma_t(v[u][i], xv[u][i], acc[i]);
