@@ -98,7 +98,7 @@ cg_residual(int32_t n, int32_t n_slices, const int64_t *sp, ColT col, const T *v
 
 // q = A p; partial p.q; last CTA: alpha = rho / (p.q).  Grid cg_pq_grid (see cgkern.cuh).
 template <typename T, int R, int L, typename ColT>
-__global__ void __launch_bounds__(kCgBlock, pq_min_ctas((int)sizeof(T) * R, sizeof(T) == 4))
+__global__ void __launch_bounds__(kCgBlock, pq_min_ctas((int)sizeof(T) * R))
 cg_spmv_pq(int32_t n, int32_t n_slices, const int64_t *sp, ColT col, const T *val,
            const T *p, T *q, double *part, CgScalars *sc) {
     // start the first slice's pointer loads while the stop flag is read, so that memory
@@ -119,7 +119,7 @@ cg_spmv_pq(int32_t n, int32_t n_slices, const int64_t *sp, ColT col, const T *va
         const int64_t slice = g / L;
         const int lane = (int)(g % L);
         T acc[R];
-        slice_rows<T, R, L, false, pq_unroll((int)sizeof(T) * R, sizeof(T) == 4)>(
+        slice_rows<T, R, L, false, pq_unroll((int)sizeof(T) * R)>(
             slice, lane, sp, col, val, p, pol, acc);
         const int64_t row0 = slice * S + (int64_t)lane * R;
         store_rows<T, R>(q, row0, n, acc);
@@ -242,8 +242,8 @@ __global__ void add_iters(CgScalars *inner, int *total) { *total += inner->iters
 // most kCgCtasPerSm CTAs per SM (the persistent kernel uses the same grid).  It depends only
 // on n and the device, so the reduction order is fixed per handle and both paths give
 // identical results; small systems use fewer CTAs and leave room for concurrent solves.
-int cg_pq_grid(int32_t n_slices, int L, int value_bytes, bool f32) {
-    const int64_t cap = (int64_t)device_facts().sm_count * pq_min_ctas(value_bytes, f32);
+int cg_pq_grid(int32_t n_slices, int L, int value_bytes) {
+    const int64_t cap = (int64_t)device_facts().sm_count * pq_min_ctas(value_bytes);
     const int64_t want = ((int64_t)n_slices * L + kCgBlock - 1) / kCgBlock;
     return (int)(want < 1 ? 1 : (want > cap ? cap : want));
 }
@@ -251,11 +251,11 @@ int cg_pq_grid(int32_t n_slices, int L, int value_bytes, bool f32) {
 // (lanes per slice, value bytes per lane entry) of the FP64 and FP32 product kernels for a
 // slice height, as with_shape picks them
 static int pq_grid64(const spmv_matrix_t A) {
-    return cg_pq_grid(A->n_slices, 32, 8 * (A->S / 32), false);
+    return cg_pq_grid(A->n_slices, 32, 8 * (A->S / 32));
 }
 static int pq_grid32(const spmv_matrix_t A) {
     const int L = A->S / 4 < 32 ? A->S / 4 : 32;
-    return cg_pq_grid(A->n_slices, L, 4 * (A->S / L), true);
+    return cg_pq_grid(A->n_slices, L, 4 * (A->S / L));
 }
 
 int cg_grid(int32_t n) {

@@ -15,18 +15,16 @@ constexpr int kCgCtasPerSm = 4;  // at most this many CTAs per SM in a CG sweep
 int cg_grid(int32_t n);
 
 // The product phase q = A p, p.q runs on a grid of its own: the sweeps' grid (at most
-// kCgCtasPerSm CTAs per SM, 64 registers) leaves the latency-bound gathers without enough
-// warps, so the product takes up to pq_min_ctas CTAs per SM (40 registers where a lane
-// holds at most 16 bytes of values per entry) and at most one slice-lane per thread.  An FP32
-// lane of at most 16 bytes instead keeps pq_unroll = 5 entries in flight (a whole row of the
-// tetrahedral meshes) at four CTAs per SM and 64 registers: measured 4.7 % faster for the
-// whole refinement solve of the 6M-row mesh than two entries at six CTAs per SM.  The
-// persistent kernel runs the same grid as virtual CTAs, so both paths stay bit-identical.
-constexpr int pq_min_ctas(int value_bytes, bool f32) {
-    return f32 && value_bytes <= 16 ? 4 : value_bytes >= 64 ? 3 : value_bytes >= 32 ? 4 : 6;
-}
-constexpr int pq_unroll(int value_bytes, bool f32) { return f32 && value_bytes <= 16 ? 5 : 2; }
-int cg_pq_grid(int32_t n_slices, int L, int value_bytes, bool f32);
+// kCgCtasPerSm CTAs per SM) leaves the latency-bound gathers without enough warps in flight.
+// A lane holding at most 16 bytes of values per entry keeps pq_unroll = 5 entries in flight
+// (a whole row of the tetrahedral meshes) at four CTAs per SM and 64 registers -- measured on
+// the 6M-row mesh against two entries at six CTAs per SM (40 registers): FP64 CG 185 -> 176 us
+// per iteration, the FP32 refinement solve 4.7 % faster; wider lanes keep two entries at
+// pq_min_ctas CTAs per SM.  The persistent kernel runs the same grid as virtual CTAs, so
+// both paths stay bit-identical.
+constexpr int pq_min_ctas(int value_bytes) { return value_bytes >= 64 ? 3 : 4; }
+constexpr int pq_unroll(int value_bytes) { return value_bytes <= 16 ? 5 : 2; }
+int cg_pq_grid(int32_t n_slices, int L, int value_bytes);
 
 // Hint: bring the line holding p into L1 without waiting for it (a later load of it hits).
 __device__ __forceinline__ void prefetch_l1(const void *p) {

@@ -239,7 +239,7 @@ static spmv_status_t run_persistent(spmv_matrix_t A, bool f32, const cg_options_
             }
             double *part = w.part.p;
             // the graph path's product grid for this shape (see cg_pq_grid)
-            int32_t Gpq = cg_pq_grid(A->n_slices, L, (int)sizeof(T) * R, sizeof(T) == 4);
+            int32_t Gpq = cg_pq_grid(A->n_slices, L, (int)sizeof(T) * R);
             int32_t pq_len = w.pq_len;
             void *args[] = {&n, &ns, &sp, &cols, &val, &x, &r, &p, &q, &dinv, &part, &Gpq,
                             &pq_len, &sc};
