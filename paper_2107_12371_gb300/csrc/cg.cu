@@ -97,7 +97,9 @@ cg_residual(int32_t n, int32_t n_slices, const int64_t *sp, ColT col, const T *v
 }
 
 // q = A p; partial p.q; last CTA: alpha = rho / (p.q).  Grid cg_pq_grid (see cgkern.cuh).
-template <typename T, int R, int L, typename ColT>
+// UU: entries in flight per lane (pq_unroll, or 2 for matrices whose widest slice needs fewer
+// load rounds that way; the per-row order, hence the result, is the same).
+template <typename T, int R, int L, typename ColT, int UU>
 __global__ void __launch_bounds__(kCgBlock, pq_min_ctas((int)sizeof(T) * R))
 cg_spmv_pq(int32_t n, int32_t n_slices, const int64_t *sp, ColT col, const T *val,
            const T *p, T *q, double *part, CgScalars *sc) {
@@ -119,8 +121,7 @@ cg_spmv_pq(int32_t n, int32_t n_slices, const int64_t *sp, ColT col, const T *va
         const int64_t slice = g / L;
         const int lane = (int)(g % L);
         T acc[R];
-        slice_rows<T, R, L, false, pq_unroll((int)sizeof(T) * R)>(
-            slice, lane, sp, col, val, p, pol, acc);
+        slice_rows<T, R, L, false, UU>(slice, lane, sp, col, val, p, pol, acc);
         const int64_t row0 = slice * S + (int64_t)lane * R;
         store_rows<T, R>(q, row0, n, acc);
 #pragma unroll
@@ -328,10 +329,17 @@ static spmv_status_t enqueue_cg64(spmv_matrix_t A, int iters, cudaStream_t st) {
         return with_shape(A->S, false, [&](auto rt, auto lt) -> spmv_status_t {
             constexpr int R = decltype(rt)::value, L = decltype(lt)::value;
             const int Gpq = pq_grid64(A);
+            constexpr int UU = pq_unroll(8 * R);
+            const bool deep = load_rounds(A->max_width, UU) < load_rounds(A->max_width, 2);
             for (int it = 0; it < iters; ++it) {
-                cg_spmv_pq<double, R, L, ColT><<<Gpq, kCgBlock, 0, st>>>(
-                    A->n, A->n_slices, A->slice_ptr.p, cols, A->sell_val.p, w.p.p, w.q.p, w.part.p,
-                    sc);
+                if (deep)
+                    cg_spmv_pq<double, R, L, ColT, UU><<<Gpq, kCgBlock, 0, st>>>(
+                        A->n, A->n_slices, A->slice_ptr.p, cols, A->sell_val.p, w.p.p, w.q.p,
+                        w.part.p, sc);
+                else
+                    cg_spmv_pq<double, R, L, ColT, 2><<<Gpq, kCgBlock, 0, st>>>(
+                        A->n, A->n_slices, A->slice_ptr.p, cols, A->sell_val.p, w.p.p, w.q.p,
+                        w.part.p, sc);
                 cg_update_xr<double><<<G, kCgBlock, 0, st>>>(A->n, w.x.p, w.r.p, w.p.p, w.q.p,
                                                              w.dinv.p, w.part.p + w.pq_len, sc);
                 cg_update_p<double><<<G, kCgBlock, 0, st>>>(A->n, w.r.p, w.dinv.p, w.p.p, sc);
@@ -351,10 +359,17 @@ static spmv_status_t enqueue_cg32(spmv_matrix_t A, int iters, cudaStream_t st) {
         return with_shape(A->S, true, [&](auto rt, auto lt) -> spmv_status_t {
             constexpr int R = decltype(rt)::value, L = decltype(lt)::value;
             const int Gpq = pq_grid32(A);
+            constexpr int UU = pq_unroll(4 * R);
+            const bool deep = load_rounds(A->max_width, UU) < load_rounds(A->max_width, 2);
             for (int it = 0; it < iters; ++it) {
-                cg_spmv_pq<float, R, L, ColT><<<Gpq, kCgBlock, 0, st>>>(
-                    A->n, A->n_slices, A->slice_ptr.p, cols, A->sell_val32.p, w.p32.p, w.q32.p,
-                    w.part.p, sc);
+                if (deep)
+                    cg_spmv_pq<float, R, L, ColT, UU><<<Gpq, kCgBlock, 0, st>>>(
+                        A->n, A->n_slices, A->slice_ptr.p, cols, A->sell_val32.p, w.p32.p,
+                        w.q32.p, w.part.p, sc);
+                else
+                    cg_spmv_pq<float, R, L, ColT, 2><<<Gpq, kCgBlock, 0, st>>>(
+                        A->n, A->n_slices, A->slice_ptr.p, cols, A->sell_val32.p, w.p32.p,
+                        w.q32.p, w.part.p, sc);
                 cg_update_xr<float><<<G, kCgBlock, 0, st>>>(A->n, w.d32.p, w.r32.p, w.p32.p,
                                                             w.q32.p, w.dinv32.p,
                                                             w.part.p + w.pq_len, sc);

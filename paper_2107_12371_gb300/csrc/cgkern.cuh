@@ -20,7 +20,8 @@ int cg_grid(int32_t n);
 // (a whole row of the tetrahedral meshes) at four CTAs per SM and 64 registers -- measured on
 // the 6M-row mesh against two entries at six CTAs per SM (40 registers): FP64 CG 185 -> 176 us
 // per iteration, the FP32 refinement solve 4.7 % faster; wider lanes keep two entries at
-// pq_min_ctas CTAs per SM.  The persistent kernel runs the same grid as virtual CTAs, so
+// pq_min_ctas CTAs per SM, and so do matrices whose widest slice needs fewer load rounds
+// that way (load_rounds).  The persistent kernel runs the same grid as virtual CTAs, so
 // both paths stay bit-identical.
 constexpr int pq_min_ctas(int value_bytes) { return value_bytes >= 64 ? 3 : 4; }
 constexpr int pq_unroll(int value_bytes) { return value_bytes <= 16 ? 5 : 2; }

@@ -28,6 +28,10 @@ struct DeviceFacts {
 };
 const DeviceFacts &device_facts();
 
+// Dependent load rounds of a row of w stored entries read in blocks of u with the rest one at a
+// time: the kernels that keep u entries in flight choose u by this count for the widest slice.
+constexpr int load_rounds(int w, int u) { return w / u + w % u; }
+
 // Status from a CUDA error code.
 inline spmv_status_t cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return SPMV_OK;

@@ -19,15 +19,17 @@ namespace {
 
 // y = A x, or with AXPBY y = alpha (A x) + beta y evaluated as fma(alpha, t, beta y) (y is not
 // read when beta == 0), t being the row sum in column order.
+// gt: the slice-lane this thread computes (slice gt / L, lane gt % L).  The entries of a row
+// go in blocks of U (all loads of a block issued before its gathers, and those before its
+// FMAs), the rest one at a time.
 template <typename T, int R, int L, int U, typename ColT, bool AXPBY>
-__device__ __forceinline__ void spmv_sell_body(int32_t n, int32_t n_slices,
+__device__ __forceinline__ void spmv_sell_body(int64_t gt, int32_t n, int32_t n_slices,
                                                const int64_t *__restrict__ sp, ColT cols,
                                                const T *__restrict__ val,
                                                const T *__restrict__ x, T *__restrict__ y,
                                                T alpha, T beta) {
     // L lanes per slice, R rows per lane: S = L R rows per slice
     constexpr int S = L * R;
-    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t slice = gt / L;
     const int lane = (int)(gt % L);
     if (slice >= n_slices) return;
@@ -85,18 +87,38 @@ __global__ void __launch_bounds__(1024)
 spmv_sell(int32_t n, int32_t n_slices, const int64_t *__restrict__ sp, ColT cols,
           const T *__restrict__ val, const T *__restrict__ x, T *__restrict__ y, T alpha,
           T beta) {
-    spmv_sell_body<T, R, L, U, ColT, AXPBY>(n, n_slices, sp, cols, val, x, y, alpha, beta);
+    spmv_sell_body<T, R, L, U, ColT, AXPBY>((int64_t)blockIdx.x * blockDim.x + threadIdx.x, n,
+                                            n_slices, sp, cols, val, x, y, alpha, beta);
 }
 
-// FP64 with one or two rows per lane, capped at 32 registers (2 x 1024 threads per SM): a
-// full SM of warps keeps enough loads in flight to stream HBM, which the 16-bit decode would
-// otherwise cost in occupancy.
+// FP64 with one or two rows per lane, capped at 32 registers (2 x 1024 threads per SM), four
+// entries in flight: for matrices whose widest slice needs fewer load rounds in blocks of four
+// than of five (see go_sell).
 template <typename T, int R, int L, int U, typename ColT, bool AXPBY>
 __global__ void __launch_bounds__(1024, 2)
 spmv_sell_occ(int32_t n, int32_t n_slices, const int64_t *__restrict__ sp, ColT cols,
               const T *__restrict__ val, const T *__restrict__ x, T *__restrict__ y, T alpha,
               T beta) {
-    spmv_sell_body<T, R, L, U, ColT, AXPBY>(n, n_slices, sp, cols, val, x, y, alpha, beta);
+    spmv_sell_body<T, R, L, U, ColT, AXPBY>((int64_t)blockIdx.x * blockDim.x + threadIdx.x, n,
+                                            n_slices, sp, cols, val, x, y, alpha, beta);
+}
+
+// FP64 with one or two rows per lane: a grid of at most kGsCtasPerSm 256-thread CTAs per SM
+// strides over the slice-lanes, each thread keeping U = 5 entries of its rows in flight (a
+// whole row of the tetrahedral meshes) at 64 registers.  Measured on the 6M-row mesh (S = 64):
+// 66.0 us, against 69.6 us for one slice-lane per thread at 32 registers and 2,048 threads per
+// SM (four entries in flight), 77.1 us with four entries and 68.3 us with two at six CTAs.
+constexpr int kGsBlock = 256;
+constexpr int kGsCtasPerSm = 4;
+template <typename T, int R, int L, int U, typename ColT, bool AXPBY>
+__global__ void __launch_bounds__(kGsBlock, kGsCtasPerSm)
+spmv_sell_gs(int32_t n, int32_t n_slices, const int64_t *__restrict__ sp, ColT cols,
+             const T *__restrict__ val, const T *__restrict__ x, T *__restrict__ y, T alpha,
+             T beta) {
+    const int64_t items = (int64_t)n_slices * L;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gt < items; gt += stride)
+        spmv_sell_body<T, R, L, U, ColT, AXPBY>(gt, n, n_slices, sp, cols, val, x, y, alpha, beta);
 }
 
 // naive CSR baseline (Sec. 4.3): the column index is read first, then x[col] from global
@@ -135,12 +157,21 @@ spmv_status_t go_sell(spmv_matrix_t A, const T *val, const T *x, T *y, T alpha, 
     const unsigned grid = grid_for((int64_t)A->n_slices * L, block);
     auto go = [&](auto c) {
         using ColT = decltype(c);
-        if constexpr (sizeof(T) == 8 && R <= 2)
-            spmv_sell_occ<T, R, L, U, ColT, AXPBY><<<grid, block, 0, st>>>(
-                A->n, A->n_slices, A->slice_ptr.p, c, val, x, y, alpha, beta);
-        else
+        if constexpr (sizeof(T) == 8 && R <= 2) {
+            if (load_rounds(A->max_width, 5) < load_rounds(A->max_width, 4)) {
+                const int64_t cap = (int64_t)device_facts().sm_count * kGsCtasPerSm;
+                const unsigned want = grid_for((int64_t)A->n_slices * L, kGsBlock);
+                const unsigned g = (int64_t)want < cap ? want : (unsigned)cap;
+                spmv_sell_gs<T, R, L, 5, ColT, AXPBY><<<g, kGsBlock, 0, st>>>(
+                    A->n, A->n_slices, A->slice_ptr.p, c, val, x, y, alpha, beta);
+            } else {
+                spmv_sell_occ<T, R, L, U, ColT, AXPBY><<<grid, block, 0, st>>>(
+                    A->n, A->n_slices, A->slice_ptr.p, c, val, x, y, alpha, beta);
+            }
+        } else {
             spmv_sell<T, R, L, U, ColT, AXPBY><<<grid, block, 0, st>>>(
                 A->n, A->n_slices, A->slice_ptr.p, c, val, x, y, alpha, beta);
+        }
     };
     if (A->index_bits == 16) go(Cols16{A->sell_col16.p, A->col_start.p});
     else go(Cols32{A->sell_col.p});
