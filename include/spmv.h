@@ -71,7 +71,10 @@ typedef enum {
 
 typedef struct {
     int slice_height;    /* S, rows per slice: 32, 64, 128 or 256 (0 = default 64)            */
-    int block;           /* threads per CTA for the SpMV kernels: 64..1024, multiple of 32 (0 = 256) */
+    int block;           /* threads per CTA for the SpMV kernels that take one slice-lane per
+                          * thread: 64..1024, multiple of 32 (0 = 256).  The FP64 kernel that
+                          * strides over the slice-lanes with five entries in flight (chosen when
+                          * the widest slice needs fewer load rounds that way) uses 256. */
     int variant;         /* SPMV_VARIANT_*                                                   */
     int reorder;         /* SPMV_REORDER_*                                                   */
     int precision;       /* SPMV_PREC_*                                                      */
