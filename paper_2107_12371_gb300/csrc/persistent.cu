@@ -84,7 +84,7 @@ template <typename T, int R, int L, typename ColT>
 __global__ void __launch_bounds__(kCgBlock, kCgCtasPerSm)
 cg_persistent(int32_t n, int32_t n_slices, const int64_t *sp, ColT col, const T *val, T *x,
               T *r, T *p, T *q, const T *dinv, double *part, int32_t Gpq, int32_t pq_len,
-              CgScalars *sc) {
+              int deep, CgScalars *sc) {
     constexpr int S = L * R;
     const uint64_t pol = policy_evict_first();
     const long long t_start = global_timer_ns();
@@ -112,7 +112,13 @@ cg_persistent(int32_t n, int32_t n_slices, const int64_t *sp, ColT col, const T 
                 const int64_t slice = g / L;
                 const int lane = (int)(g % L);
                 T acc[R];
-                slice_rows<T, R, L, true>(slice, lane, sp, col, val, p, pol, acc);
+                // entries in flight as in the graph path's product (the order, hence the
+                // result, is the same either way)
+                if (deep)
+                    slice_rows<T, R, L, true, pq_unroll((int)sizeof(T) * R)>(slice, lane, sp, col,
+                                                                           val, p, pol, acc);
+                else
+                    slice_rows<T, R, L, true>(slice, lane, sp, col, val, p, pol, acc);
                 const int64_t row0 = slice * S + (int64_t)lane * R;
                 store_rows<T, R>(q, row0, n, acc);
 #pragma unroll
@@ -241,8 +247,10 @@ static spmv_status_t run_persistent(spmv_matrix_t A, bool f32, const cg_options_
             // the graph path's product grid for this shape (see cg_pq_grid)
             int32_t Gpq = cg_pq_grid(A->n_slices, L, (int)sizeof(T) * R);
             int32_t pq_len = w.pq_len;
+            constexpr int UU = pq_unroll((int)sizeof(T) * R);
+            int deep = load_rounds(A->max_width, UU) < load_rounds(A->max_width, 2) ? 1 : 0;
             void *args[] = {&n, &ns, &sp, &cols, &val, &x, &r, &p, &q, &dinv, &part, &Gpq,
-                            &pq_len, &sc};
+                            &pq_len, &deep, &sc};
             GB_CUDA(cudaLaunchCooperativeKernel((const void *)kern, dim3(w.pers_grid),
                                                 dim3(kCgBlock), args, 0, st));
             GB_CUDA(cudaMemcpyAsync(w.h_scal, w.scal.p, 2 * sizeof(CgScalars),
