@@ -501,7 +501,8 @@ def test_spmm_16_byte_aligned_blocks(oracle, k, dtype):
     assert np.array_equal(Yd.cpu().numpy(), ref)
 
 
-@pytest.mark.parametrize("k,dtype", [(8, np.float64), (32, np.float64), (32, np.float32)])
+@pytest.mark.parametrize("k,dtype", [(8, np.float64), (32, np.float64), (8, np.float32),
+                                     (32, np.float32)])
 def test_spmm_full_size_parity(oracle, k, dtype):
     """The SpMM workload of the benchmark at full size -- mixed hexahedron / prism /
     tetrahedron mesh of 87^3 hexahedra (about 1.98M cells), RCM and sigma = 1024 sorting, 16-bit
