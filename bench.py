@@ -793,7 +793,8 @@ def _make_request(args):
 def serving_results(args, capi, torch):
     """A bounded sample of the serving stream: the first n requests of the 2,000-request
     stream (cell counts log-uniform in [1e4, 2e6], seed = request index, FP64 or mixed
-    precision by a seeded coin, rtol 1e-8), solved (a) one at a time through cg_solve and (b)
+    precision by a seeded coin, rtol 1e-8), solved (a) one at a time through cg_solve (and again
+    all as plain FP64 solves, the baseline of the served rates) and (b)
     through the server with Poisson arrivals at 0.5x, 1x and 2x the one-at-a-time rate, and
     all submitted at once (its capacity), 60 GB budget.  Latency = arrival to result in host
     memory (conversion included)."""
@@ -808,9 +809,11 @@ def serving_results(args, capi, torch):
     cells = [r[1] for r in reqs]
     # (a) one at a time; a first untimed pass loads every kernel the stream uses (lazy module
     # loading makes a kernel's first launch slow) and warms the allocator
-    def one_at_a_time():
+    def one_at_a_time(plain_fp64=False):
         lat = []
         for (i, n, rp, ci, v, b), o in zip(reqs, opts):
+            if plain_fp64:
+                o = capi.cg_default_options(rtol=1e-8, mixed=0)
             t0 = time.perf_counter()
             A = capi.Matrix(n, rp, ci, v, precision=capi.SPMV_PREC_DUAL if o.mixed else 0)
             bd = torch.from_numpy(b).cuda()
@@ -826,6 +829,10 @@ def serving_results(args, capi, torch):
     lat_serial = one_at_a_time()
     t_serial = time.perf_counter() - t_all
     rate_serial = n_req / t_serial
+    # the same requests as plain FP64 solves, one at a time (the baseline of the served rates)
+    t_all = time.perf_counter()
+    lat_plain = one_at_a_time(plain_fp64=True)
+    rate_plain = n_req / (time.perf_counter() - t_all)
     # (b) served, Poisson arrivals at 0.5x, 1x and 2x the one-at-a-time rate, and every
     # request submitted at once (the server's capacity)
     served = {}
@@ -870,7 +877,10 @@ def serving_results(args, capi, torch):
         **served,
         "one_at_a_time": {"solves_per_s": rate_serial,
                           "p50_latency_s": float(np.percentile(lat_serial, 50)),
-                          "p99_latency_s": float(np.percentile(lat_serial, 99))}}}
+                          "p99_latency_s": float(np.percentile(lat_serial, 99))},
+        "one_at_a_time_plain_fp64": {"solves_per_s": rate_plain,
+                                     "p50_latency_s": float(np.percentile(lat_plain, 50)),
+                                     "p99_latency_s": float(np.percentile(lat_plain, 99))}}}
 
 
 def main():
