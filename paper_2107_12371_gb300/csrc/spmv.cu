@@ -1,4 +1,4 @@
-// spmv.cu -- SpMV / SpMM kernels.
+// spmv.cu -- SpMV kernels (the multi-vector products are in spmm.cu).
 //
 // spmv_sell<T, R, L>: L lanes per slice of S = L R rows, lane l owns rows l R .. l R + R - 1
 //   of the slice.  Because a slice is stored column-major (Sec. 4.2), step t of the lanes
@@ -10,6 +10,10 @@
 //   are skipped.  Column indices come as int32 or (when every slice spans fewer than 65,535
 //   columns) as 16-bit offsets from the slice's col_start (Sec. 5.1), 10 instead of 12 bytes
 //   per FP64 non-zero.
+// spmv_sell_occ / spmv_sell_gs: the FP64 forms with one or two rows per lane, one slice-lane
+//   per thread at 32 registers, or a grid of four CTAs per SM striding over the slice-lanes
+//   with five entries of each row in flight; the one whose widest slice needs fewer dependent
+//   load rounds is launched.
 // spmv_csr: the naive baseline of Sec. 4.3, thread per CSR row.
 #include "common.cuh"
 #include "ptx.cuh"
