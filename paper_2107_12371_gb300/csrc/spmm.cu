@@ -104,11 +104,6 @@ spmm_sell(int32_t n, int32_t S, int32_t n_slices, int k, const int64_t *__restri
 template <typename T, int VW>
 struct VecOf;
 template <>
-struct VecOf<double, 1> {
-    static __device__ __forceinline__ void load(const double *p, double (&v)[1]) { v[0] = __ldg(p); }
-    static __device__ __forceinline__ void store(double *p, const double (&v)[1]) { p[0] = v[0]; }
-};
-template <>
 struct VecOf<double, 2> {
     static __device__ __forceinline__ void load(const double *p, double (&v)[2]) {
         const double2 t = __ldg(reinterpret_cast<const double2 *>(p));
@@ -117,17 +112,6 @@ struct VecOf<double, 2> {
     }
     static __device__ __forceinline__ void store(double *p, const double (&v)[2]) {
         *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
-    }
-};
-template <>
-struct VecOf<float, 2> {
-    static __device__ __forceinline__ void load(const float *p, float (&v)[2]) {
-        const float2 t = __ldg(reinterpret_cast<const float2 *>(p));
-        v[0] = t.x;
-        v[1] = t.y;
-    }
-    static __device__ __forceinline__ void store(float *p, const float (&v)[2]) {
-        *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
     }
 };
 template <>
