@@ -33,8 +33,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "SpMV effective GB/s (% HBM peak) FP64 vs mixed; served CG solves/s, p99"
 WORKLOAD = "kuhn-tet 100^3 FV Laplacian, Dirichlet, 6,000,000 rows, 29,880,000 nnz, RCM order"
-FLUSH_BYTES = 512 << 20
-VARIANTS = {0: "auto", 1: "spmv_csr", 2: "spmv_sell", 3: "spmv_sell_window", 4: "spmv_sell_bulk"}  # 256 MB written + 256 MB read between timed steps
+FLUSH_BYTES = 512 << 20  # 256 MB written + 256 MB read between timed steps
+VARIANTS = {0: "auto", 1: "spmv_csr", 2: "spmv_sell", 3: "spmv_sell_window", 4: "spmv_sell_bulk"}
 
 
 def spmv_bytes(n, nnz, f32=False):
