@@ -218,9 +218,10 @@ spmv_status_t spmv_apply_csr(spmv_matrix_t A, const double *x_dev, double *y_dev
 /*
  * spmv_apply_multi -- async.  Y = A X for k right-hand sides, X and Y row-major
  * (n_rows x k, entry (i, c) at i*k + c), device memory, FP64, 16-byte aligned, not
- * overlapping.  1 <= k <= 64.  Each gathered row of X is reused for all k columns (power-of-two
- * k are gathered with 16-byte vector loads).  Column c equals spmv_apply on column c bit for
- * bit.
+ * overlapping.  1 <= k <= 64.  Each gathered row of X is reused for all k columns: when k is a
+ * power-of-two multiple of 32 bytes and X and Y are 32-byte aligned, each lane gathers 32 bytes
+ * of a row with one 256-bit load; other power-of-two k use 8- or 16-byte vector loads.  Column
+ * c equals spmv_apply on column c bit for bit.
  */
 spmv_status_t spmv_apply_multi(spmv_matrix_t A, int k, const double *X_dev, double *Y_dev,
                                void *stream);
