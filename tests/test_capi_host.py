@@ -110,3 +110,26 @@ def test_entry_points_reject_null_handles(lib):
     assert L.spmv_device_status(None, None) == capi.SPMV_ERR_INVALID_ARG
     assert L.spmv_diag_bulk_timeout(None, None) == capi.SPMV_ERR_INVALID_ARG
     assert L.spmv_server_destroy(None) == capi.SPMV_OK
+
+
+def test_binding_constants_match_the_header():
+    """Every #define SPMV_* constant of the header that the binding names has the same value
+    there, so the binding cannot drift from the C ABI."""
+    src = open(os.path.join(ROOT, "include", "spmv.h")).read()
+    defines = {name: int(val) for name, val in
+               re.findall(r"^#define\s+(SPMV_[A-Z0-9_]+)\s+(-?\d+)", src, flags=re.M)}
+    enums = dict(re.findall(r"\b(SPMV_(?:OK|ERR_[A-Z_]+))\s*=\s*(\d+)", src))
+    checked = 0
+    for name in dir(capi):
+        if not name.startswith("SPMV_"):
+            continue
+        val = getattr(capi, name)
+        if name in defines:
+            assert val == defines[name], name
+            checked += 1
+        elif name in enums:
+            assert val == int(enums[name]), name
+            checked += 1
+    assert checked >= 20
+    for name in ("SPMV_VARIANT_SELL_BULK", "SPMV_PREC_DUAL", "SPMV_REORDER_RCM"):
+        assert name in defines and hasattr(capi, name)
