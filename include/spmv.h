@@ -352,18 +352,23 @@ spmv_status_t spmv_diag_barrier_timeout(int ctas, double limit_s, void *stream);
  * thread-per-row CSR product) directly on caller-owned device CSR arrays, and calls no
  * cudaMalloc, cudaFree or other allocating routine.  Its work vectors and reduction scratch
  * live in one fixed array inside the library (4 * SPMV_NOALLOC_MAX_ROWS doubles plus about
- * 33 KB of partial sums and scalars, about 2.1 MB), which every GPU that loads the library
- * holds until the process exits.
+ * 33 KB of partial sums and scalars, about 2.1 MB).
  *   n <= SPMV_NOALLOC_MAX_ROWS, else SPMV_ERR_INVALID_ARG with no device work.  row_ptr_dev,
  *   col_idx_dev, values_dev: device CSR with the layout and checks of spmv_create (checked on
- *   the device: SPMV_ERR_INVALID_CSR; a zero or missing diagonal is also INVALID_CSR).
- *   b_dev, x_dev: device double[n]; x_dev holds x0 when opt->use_x0, else it is overwritten
- *   starting from 0.  opt->mixed and opt->persistent give SPMV_ERR_UNSUPPORTED.
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.  All calls share the
- * one array, which keeps the last call's contents; each call clears what it needs at its
- * start.  Calls that overlap on the GPU (other streams, other host threads) race on the array
- * and must be serialised by the caller.
+ *   the device: SPMV_ERR_INVALID_CSR, x untouched; a zero or missing diagonal is also
+ *   INVALID_CSR).  b_dev, x_dev: device double[n]; x_dev holds x0 when opt->use_x0, else it is
+ *   overwritten starting from 0.  opt->mixed and opt->persistent give SPMV_ERR_UNSUPPORTED.
+ *   The call returns after the solve is complete (it waits on `stream`).
+ * Set-up: the first call on a device (and the first after that device's context is replaced,
+ * e.g. by cudaDeviceReset) looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current.  With the CUDA runtime's default lazy module loading, that first call
+ * is also when the device reserves the array's 2.1 MB, which it then holds until the process
+ * exits (with CUDA_MODULE_LOADING=EAGER it is reserved when the library is loaded).  A call
+ * with n = 0 performs the set-up alone and returns SPMV_OK: make it on each device before the
+ * application pools the device's memory, and before any stream capture begins.
+ * All calls share the one array, which keeps the last call's contents; each call clears what
+ * it needs at its start.  Calls that overlap on the GPU (other streams, other host threads)
+ * race on the array and must be serialised by the caller.
  */
 spmv_status_t cg_solve_csr_noalloc(int32_t n, int64_t nnz, const int32_t *row_ptr_dev,
                                    const int32_t *col_idx_dev, const double *values_dev,

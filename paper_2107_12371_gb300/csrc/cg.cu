@@ -167,8 +167,8 @@ cg_update_xr(int32_t n, T *x, T *r, const T *p, const T *q, const T *dinv, doubl
         sc->rr = tot[1];
         sc->iters += 1;
         if (tot[1] <= sc->tol2 * sc->bb) sc->done = 1;
-        else if (sc->iters >= sc->max_iter) sc->done = 2;
         else if (!isfinite(tot[1])) sc->done = 3;
+        else if (sc->iters >= sc->max_iter) sc->done = 2;
     }
 }
 

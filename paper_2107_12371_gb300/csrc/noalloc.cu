@@ -5,12 +5,17 @@
 // application that owns and pools all GPU memory itself, a real-time loop whose memory is
 // fixed up front, or code running where a cudaMalloc would synchronise the device or fail.
 // For them the work vectors and reduction scratch of this solve live in one file-scope
-// __device__ array of fixed size, created when the library is loaded and held by every GPU
-// that loads it until the process exits.  Systems up to kNoallocMaxRows rows fit.
+// __device__ array of fixed size (about 2.1 MB).  The array belongs to this file's module:
+// with the CUDA runtime's default lazy module loading it is reserved on a device by the first
+// call on that device (the set-up below, which a call with n = 0 performs alone), or when the
+// library is loaded if CUDA_MODULE_LOADING=EAGER; from then on the device holds it until the
+// process exits.  Systems up to kNoallocMaxRows rows fit.
 //
 // The iteration is the one of cg_solve (Jacobi-preconditioned CG, last-CTA reductions in a
 // fixed order, true-residual check with at most two restarts), with a thread-per-row CSR
 // product instead of the sliced-ELLPACK one.
+#include <cuda.h>
+
 #include <chrono>
 #include <climits>
 #include <cmath>
@@ -50,18 +55,56 @@ Scratch carve(double *base) {
     return s;
 }
 
-// device address of the scratch array, resolved once per device with that device current
+// Identity of the current CUDA context (cuCtxGetCurrent + cuCtxGetId, fetched from the driver
+// through the runtime so the library does not link the driver library itself).  A context
+// created after cudaDeviceReset gets a new identity, so an address resolved in an earlier
+// context is never reused.  Returns false when the driver does not offer the two calls.
+bool current_context_id(unsigned long long *id) {
+    using GetCurrent = CUresult (*)(CUcontext *);
+    using GetId = CUresult (*)(CUcontext, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+        void *f1 = nullptr, *f2 = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault,
+                                             &q1) == cudaSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) ==
+                cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess) {
+            get_current = (GetCurrent)f1;
+            get_id = (GetId)f2;
+        }
+        cudaGetLastError();
+    });
+    if (!get_current || !get_id) return false;
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+    return get_id(ctx, id) == CUDA_SUCCESS;
+}
+
+// Set-up: the device address of the scratch array, resolved with cudaGetSymbolAddress with the
+// caller's device current, once per device and context (re-resolved when the context changes,
+// e.g. after cudaDeviceReset; resolved on every call if the context cannot be identified).
 spmv_status_t scratch_address(double **out) {
     static std::mutex mu;
     static double *addr[64] = {};
+    static unsigned long long ctx_of[64] = {};
     int dev = 0;
     GB_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return SPMV_ERR_UNSUPPORTED;
+    // make the device's context current (cudaSetDevice initialises it), so that it can be
+    // identified before the lookup
+    GB_CUDA(cudaSetDevice(dev));
+    unsigned long long ctx = 0;
+    const bool known = current_context_id(&ctx);
     std::lock_guard<std::mutex> lock(mu);
-    if (!addr[dev]) {
+    if (!known || !addr[dev] || ctx_of[dev] != ctx) {
         void *p = nullptr;
         GB_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
         addr[dev] = (double *)p;
+        ctx_of[dev] = known ? ctx : 0;
     }
     *out = addr[dev];
     return SPMV_OK;
@@ -184,8 +227,8 @@ na_update_xr(int32_t n, double *x, double *r, const double *p, const double *q,
         sc->rr = tot[1];
         sc->iters += 1;
         if (tot[1] <= sc->tol2 * sc->bb) sc->done = 1;
-        else if (sc->iters >= sc->max_iter) sc->done = 2;
         else if (!isfinite(tot[1])) sc->done = 3;
+        else if (sc->iters >= sc->max_iter) sc->done = 2;
     }
 }
 
@@ -230,11 +273,11 @@ extern "C" spmv_status_t cg_solve_csr_noalloc(int32_t n, int64_t nnz, const int3
     if (!(o.rtol >= 0.0) || o.max_iter < 1 || o.check_every < 0 || o.timeout_s < 0)
         return SPMV_ERR_INVALID_ARG;
     if (o.mixed || o.persistent) return (res->status = SPMV_ERR_UNSUPPORTED);
-    if (n == 0) return (res->status = SPMV_OK);
     cudaStream_t st = (cudaStream_t)stream;
     double *base = nullptr;
-    spmv_status_t s = scratch_address(&base);
+    spmv_status_t s = scratch_address(&base);  // set-up (also for n == 0)
     if (s != SPMV_OK) return (res->status = s);
+    if (n == 0) return (res->status = SPMV_OK);
     const Scratch w = carve(base);
     int G = device_facts().sm_count * 2;
     if (G > kNoallocMaxGrid) G = kNoallocMaxGrid;
@@ -255,8 +298,7 @@ extern "C" spmv_status_t cg_solve_csr_noalloc(int32_t n, int64_t nnz, const int3
         CgScalars h{};
         int hflags = 0;
         GB_TRY(read_back(w.sc, w.flags, &h, &hflags, st));
-        if (hflags & 15) return (res->status = SPMV_ERR_INVALID_CSR);
-        if (hflags & 16) return (res->status = SPMV_ERR_INVALID_CSR);
+        if (hflags & 31) return (res->status = SPMV_ERR_INVALID_CSR);
         na_residual<<<G, kCgBlock, 0, st>>>(n, row_ptr, col_idx, values, x, o.use_x0 ? 0 : 1, b,
                                             w.r, w.p, w.dinv, w.part, w.sc);
         GB_LAUNCHED();

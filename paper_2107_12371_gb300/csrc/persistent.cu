@@ -162,8 +162,8 @@ cg_persistent(int32_t n, int32_t n_slices, const int64_t *sp, ColT col, const T 
         rho = t2[0];
         ++iters;
         if (t2[1] <= tol2 * bb) done = 1;
-        else if (iters >= max_iter) done = 2;
         else if (!isfinite(t2[1])) done = 3;
+        else if (iters >= max_iter) done = 2;
         if (done) {
             if (blockIdx.x == 0 && threadIdx.x == 0) sc->rr = t2[1];
             break;

@@ -672,17 +672,28 @@ def test_c2_full_size_parity(oracle, reorder, bits, variant):
     A.apply(xi, yi)
     torch.cuda.synchronize()
     rp, ci, v = capi.spmv_export_csr(A.handle, m.n, m.nnz)
-    xin = xi.cpu().numpy()
-    mi = meshgen.CsrMatrix(m.n, rp, ci, v)
-    check_fp64(mi, xin, yi.cpu().numpy(), oracle)
+    # the renumbered matrix P A P^T, built by the oracle from the original CSR with the
+    # oracle's own (R)CM order, equals the handle's bit for bit (Sec. 4.1: reordering only
+    # renumbers; every coefficient keeps its value)
     if reorder == capi.SPMV_REORDER_RCM:
-        perm = A.permutation()
         ref_perm = oracle.cm_order(m.row_ptr, m.col_idx)
-        assert np.array_equal(perm, ref_perm)
+        assert np.array_equal(A.permutation(), ref_perm)
+        ro, co, vo = oracle.permute_csr(m.row_ptr, m.col_idx, m.values, ref_perm)
         assert A.info()["bandwidth"] < m.n // 20
+    else:
+        ref_perm = np.arange(m.n, dtype=np.int32)
+        ro, co, vo = m.row_ptr, m.col_idx, m.values
+    assert np.array_equal(rp, ro) and np.array_equal(ci, co)
+    assert np.array_equal(v.view(np.uint64), np.asarray(vo).view(np.uint64))
+    # the product against the oracle's SpMV of the oracle's matrix, x renumbered by the
+    # oracle's permutation
+    xin = x[ref_perm]
+    assert np.array_equal(xi.cpu().numpy(), xin)
+    mi = meshgen.CsrMatrix(m.n, ro, co, vo)
+    check_fp64(mi, xin, yi.cpu().numpy(), oracle)
     # FP32 product of the same handle against the FP32 oracle
     x32 = xin.astype(np.float32)
     y32 = gpu_spmv(A, x32, f32=True)
-    ref32 = oracle.spmv_f32(rp, ci, v.astype(np.float32), x32, use_fma=True)
+    ref32 = oracle.spmv_f32(ro, co, np.asarray(vo).astype(np.float32), x32, use_fma=True)
     assert np.array_equal(y32, ref32)
     assert capi.spmv_device_status(A.handle) == capi.SPMV_OK

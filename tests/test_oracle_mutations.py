@@ -40,6 +40,11 @@ MUTATIONS = [
      "if (!any || c + 1 > hi) hi = c + 1;", "if (!any || c > hi) hi = c;"),
     ("refinement update of x without the residual's scale",
      "x[i] = x[i] + s * (double)d[i];", "x[i] = x[i] + (double)d[i];"),
+    ("adaptive inner tolerance with ||r|| / ||b|| instead of ||b|| / ||r||",
+     "double need = 0.5 * rtol * bnorm / rnorm;", "double need = 0.5 * rtol * rnorm / bnorm;"),
+    ("adaptive inner tolerance capped with max instead of min",
+     "if (need > tol_in) tol_in = need < 0.5 ? need : 0.5;",
+     "if (need > tol_in) tol_in = need > 0.5 ? need : 0.5;"),
 ]
 
 

@@ -583,3 +583,81 @@ def test_mixed_ir_reaches_fp64_residual(oracle, adaptive):
     assert res <= 1e-10
     ref = np.linalg.solve(A, b)
     assert np.linalg.norm(x - ref) <= np.linalg.cond(A) * 1e-10 * np.linalg.norm(ref)
+
+
+def _jacobi_pcg_dense(A, rhs, tol, cap):
+    """Textbook Jacobi-preconditioned CG in FP64 on a dense matrix (numpy products), from
+    x = 0: returns (iterations until ||r|| <= tol ||rhs||, capped at cap; the iterate)."""
+    dinv = 1.0 / np.diag(A)
+    x = np.zeros_like(rhs)
+    r = rhs.copy()
+    z = dinv * r
+    p = z.copy()
+    rho = r @ z
+    nb = np.linalg.norm(rhs)
+    for it in range(1, cap + 1):
+        q = A @ p
+        a = rho / (p @ q)
+        x += a * p
+        r -= a * q
+        if np.linalg.norm(r) <= tol * nb:
+            return it, x
+        z = dinv * r
+        rho_new = r @ z
+        p = z + (rho_new / rho) * p
+        rho = rho_new
+    return cap, x
+
+
+def _adaptive_inner_tol(rtol, inner_rtol, bnorm, rnorm):
+    """Inner tolerance of a refinement step, as the reading of the refinement defines it: the
+    reduction the outer residual still needs with a factor 2 of margin, at least inner_rtol and
+    at most 1/2."""
+    return max(inner_rtol, min(0.5, 0.5 * rtol * bnorm / rnorm))
+
+
+def test_mixed_ir_adaptive_inner_tolerance_first_step(oracle):
+    """With rtol = 1e-3 and inner_rtol = 1e-6 the adaptive rule sets the first inner tolerance to
+    0.5 rtol = 5e-4 (r = b at the first step): one refinement step whose inner solve takes as
+    many iterations as textbook FP64 Jacobi-PCG needs to reduce its residual by 5e-4 (within one,
+    for the FP32 rounding); without the rule the inner solve runs to 1e-6."""
+    m, rng = meshgen.kuhn_tet_matrix(5, seed=4, dirichlet=True)
+    b = meshgen.uniform_vectors(rng, m.n)
+    A = m.to_dense()
+    tol1 = _adaptive_inner_tol(1e-3, 1e-6, 1.0, 1.0)
+    m1, _ = _jacobi_pcg_dense(A, b, tol1, 1000)
+    _, info = oracle.mixed_ir(m.row_ptr, m.col_idx, m.values, b, rtol=1e-3, inner_rtol=1e-6,
+                              adaptive=True)
+    assert info["converged"] and info["outer_iterations"] == 1
+    assert abs(info["inner_iterations"] - m1) <= 1
+    m_fixed, _ = _jacobi_pcg_dense(A, b, 1e-6, 1000)
+    assert m_fixed > m1 + 5
+    _, info = oracle.mixed_ir(m.row_ptr, m.col_idx, m.values, b, rtol=1e-3, inner_rtol=1e-6,
+                              adaptive=False)
+    assert info["outer_iterations"] == 1 and abs(info["inner_iterations"] - m_fixed) <= 1
+
+
+def test_mixed_ir_adaptive_inner_tolerance_second_step(oracle):
+    """The rule's ratio ||b|| / ||r||: the first inner solve is capped at j iterations (j chosen
+    so that textbook FP64 PCG leaves a relative residual rho1 < 3e-3), so the second step starts
+    from ||r1|| = rho1 ||b|| and must stop at max(1e-7, min(1/2, 0.5 rtol / rho1)) -- a loose
+    tolerance that a fresh PCG on r1 / ||r1|| reaches in m2 < j iterations.  Expected: two
+    refinement steps and j + m2 inner iterations (within one).  Taking ||r|| / ||b|| instead of
+    ||b|| / ||r||, or max instead of min, changes the second step's count."""
+    m, rng = meshgen.kuhn_tet_matrix(5, seed=4, dirichlet=True)
+    b = meshgen.uniform_vectors(rng, m.n)
+    A = m.to_dense()
+    rtol, inner_rtol = 1e-4, 1e-7
+    j = next(k for k in range(1, 200)
+             if np.linalg.norm(b - A @ _jacobi_pcg_dense(A, b, 0.0, k)[1]) < 3e-3 * np.linalg.norm(b))
+    _, xj = _jacobi_pcg_dense(A, b, 0.0, j)
+    r1 = b - A @ xj
+    rho1 = np.linalg.norm(r1) / np.linalg.norm(b)
+    tol2 = _adaptive_inner_tol(rtol, inner_rtol, np.linalg.norm(b), np.linalg.norm(r1))
+    assert inner_rtol < tol2 < 0.5 and rho1 > 2 * rtol  # the rule is active at step 2
+    m2, _ = _jacobi_pcg_dense(A, r1 / np.linalg.norm(r1), tol2, 1000)
+    assert m2 + 2 < j  # the second inner solve stops on its tolerance, not on the cap
+    _, info = oracle.mixed_ir(m.row_ptr, m.col_idx, m.values, b, rtol=rtol, inner_rtol=inner_rtol,
+                              inner_max_iter=j, adaptive=True)
+    assert info["converged"] and info["outer_iterations"] == 2
+    assert abs(info["inner_iterations"] - (j + m2)) <= 1
