@@ -330,6 +330,31 @@ spmv_status_t cg_solve(spmv_matrix_t A, const double *b_dev, double *x_dev, cons
                        cg_result_t *result, void *stream);
 
 /*
+ * cg_solve_multi -- sync.  Solves A X = B for k right-hand sides at once: k Jacobi-PCG
+ * recurrences (FP64, or with opt->mixed the FP32-inner / FP64 refinement of cg_solve, with the
+ * same inner tolerance rule) advanced in lock-step, each iteration one multi-vector product
+ * Q = A P in which every streamed matrix entry gathers one row of P for all k columns.  Not in
+ * the paper, whose linear solver is SpMV-bound (Sec. 2): batching the systems that share a
+ * matrix reads the matrix once per iteration instead of k times.  Each column keeps its own
+ * step lengths and its own stop (a converged column keeps its x and drops out of the updates)
+ * and restarts from its true residual as cg_solve does (at most twice).
+ *   k: 1..32.  B_dev, X_dev: device double[n_rows * k], row-major (entry (i, c) at i*k + c),
+ *   internal numbering, not overlapping.  X holds x0 when opt->use_x0, else it is
+ *   overwritten (the solve starts from 0).  results: cg_result_t[k] (may be NULL): per column
+ *   the iterations (mixed: inner iterations in total), the restarts (mixed: refinement steps),
+ *   the true relative residual recomputed in FP64, and the column's status.
+ *   opt->persistent: each recurrence runs as one cooperative kernel instead of CUDA-graph
+ *   batches of check_every iterations; the results are identical bit for bit.
+ * Returns SPMV_OK when every column converged, else the first failing column's status
+ * (NOT_CONVERGED, TIMEOUT); INVALID_ARG, UNSUPPORTED (no FP64 values; mixed without FP32
+ * values), OOM, CUDA as cg_solve.  The handle keeps the work arrays (five of n_rows * kp
+ * doubles, kp = k rounded up to 8, 16 or 32, plus four of n_rows * kp floats for mixed),
+ * counted in device_bytes.
+ */
+spmv_status_t cg_solve_multi(spmv_matrix_t A, int k, const double *B_dev, double *X_dev,
+                             const cg_options_t *opt, cg_result_t *results, void *stream);
+
+/*
  * spmv_diag_barrier_timeout -- sync.  Self-test of the failure path of the persistent CG
  * kernel's bounded waits (not in the paper): launches `ctas` co-resident CTAs (1 <= ctas <= SM
  * count) on the kernel's grid barrier configured to expect one CTA more than exist, so no
@@ -390,6 +415,9 @@ typedef struct {
 } spmv_server_stats_t;
 
 /* Creates a server with a device-memory budget (bytes) and at most max_slots solves in flight.
+ * Admission: a free slot takes the first queued request (in arrival order) whose estimated
+ * footprint fits what the budget has left, so a large request waiting for memory does not
+ * block smaller ones behind it; a request passed over 16 times is admitted next.
  * The server allocates from a stream-ordered memory pool of its own that keeps up to the
  * budget mapped after requests free it (released when the server is destroyed). */
 spmv_status_t spmv_server_create(size_t hbm_budget_bytes, int max_slots, spmv_server_t *out);

@@ -110,6 +110,8 @@ _SIGS = {
     "spmv_permute": [_P, _int, _int, _P, _P, _P],
     "cg_default_options": [ctypes.POINTER(cg_options_t)],
     "cg_solve": [_P, _P, _P, ctypes.POINTER(cg_options_t), ctypes.POINTER(cg_result_t), _P],
+    "cg_solve_multi": [_P, _int, _P, _P, ctypes.POINTER(cg_options_t),
+                       ctypes.POINTER(cg_result_t), _P],
     "spmv_diag_barrier_timeout": [_int, ctypes.c_double, _P],
     "cg_solve_csr_noalloc": [_i32, _i64, _P, _P, _P, _P, _P, ctypes.POINTER(cg_options_t),
                              ctypes.POINTER(cg_result_t), _P],
@@ -383,6 +385,18 @@ def cg_solve(h, b, x, options=None, stream=None, raise_on_error=True):
     return out
 
 
+def cg_solve_multi(h, k, B, X, options=None, stream=None):
+    """k right-hand sides in lock-step; B, X row-major n x k device tensors.  Returns
+    (status, [per-column result dicts])."""
+    opt = options if options is not None else cg_default_options()
+    res = (cg_result_t * int(k))()
+    st = load().cg_solve_multi(h, int(k), _ptr(B), _ptr(X), ctypes.byref(opt), res,
+                               _stream(stream))
+    cols = [dict(iterations=r.iterations, outer_iterations=r.outer_iterations,
+                 rel_residual=r.rel_residual, status=r.status) for r in res]
+    return st, cols
+
+
 SPMV_NOALLOC_MAX_ROWS = 65536
 
 
@@ -492,6 +506,11 @@ class Matrix:
 
     def solve(self, b, x, stream=None, raise_on_error=True, **cg_opts):
         return cg_solve(self.handle, b, x, cg_default_options(**cg_opts), stream, raise_on_error)
+
+    def solve_multi(self, B, X, stream=None, **cg_opts):
+        """B, X: n x k row-major device tensors; returns (status, per-column results)."""
+        return cg_solve_multi(self.handle, B.shape[1], B, X, cg_default_options(**cg_opts),
+                              stream)
 
     def close(self):
         if getattr(self, "handle", None):

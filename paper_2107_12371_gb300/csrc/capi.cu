@@ -383,10 +383,12 @@ spmv_status_t spmv_permute(spmv_matrix_t A, int direction, int elem_bytes, const
 namespace gb {
 
 void release_cg(spmv_matrix_t A);
+void release_mcg(spmv_matrix_t A);
 
 void release_matrix(spmv_matrix_t A) {
     size_t *t = &A->bytes;
     release_cg(A);
+    release_mcg(A);
     for (auto &h : A->h_stage) {
         h.x.release(t);
         h.y.release(t);

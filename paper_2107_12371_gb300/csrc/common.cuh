@@ -136,6 +136,8 @@ struct CgWork {
     int pers_grid = 0;
 };
 
+struct McgWork;  // multi-right-hand-side CG work (mcg.cu)
+
 }  // namespace gb
 
 struct spmv_matrix_s {
@@ -172,6 +174,8 @@ struct spmv_matrix_s {
     gb::DevBuf<int32_t> bulk_part;   // CTA b takes slices [bulk_part[b], bulk_part[b + 1])
     gb::DevBuf<int> dev_status;      // bit 0: a staged product gave up a bounded wait
     gb::CgWork cg;
+    gb::McgWork *mcg = nullptr;  // created by the first cg_solve_multi
+    int mcg_bytes = 32;          // cg_solve_multi: bytes of a row each product lane gathers
 
     // spmv_apply_host(_async): two staging sets used in turn, each with device copies of x and
     // y, two streams of its own (product, device-to-host) and events; created on first use

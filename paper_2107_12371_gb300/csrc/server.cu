@@ -1,10 +1,13 @@
 // server.cu -- continuous-batching CG solve server.
 //
-// Requests (a CSR system and a right-hand side, copied at submit) wait in a FIFO queue.  A
-// request is admitted as soon as a slot is free and its estimated device footprint fits in
-// what the memory budget has left; its solve then runs on the slot's own CUDA stream, so the
-// kernels of all admitted solves overlap on the GPU while new requests keep arriving.  A slot
-// takes the next request the moment its solve finishes (no batch boundaries).  Each solve
+// Requests (a CSR system and a right-hand side, copied at submit) wait in a queue in arrival
+// order.  A free slot admits the first queued request whose estimated device footprint fits
+// in what the memory budget has left, so a large request waiting for memory does not hold up
+// smaller ones behind it; a request that has been passed over kMaxBypass times is admitted
+// next (admission waits for it), so none starves.  Its solve then runs on the slot's own CUDA
+// stream, so the kernels of all admitted solves overlap on the GPU while new requests keep
+// arriving.  A slot takes the next request the moment its solve finishes (no batch
+// boundaries).  Each solve
 // keeps its matrix, vectors and CG state in HBM until it completes; only x returns to the
 // host.  Every per-problem kernel uses the same fixed grid and reduction order whatever else
 // runs, so a result is bit-identical alone and in a mix.
@@ -42,8 +45,12 @@ struct Request {
     size_t est_bytes = 0;
     Clock::time_point t_submit, t_start, t_done;
     double setup_s = 0, solve_s = 0, teardown_s = 0;
+    int bypassed = 0;  // times a later request was admitted before this one
     bool done = false;
 };
+
+// admissions of later requests that a queued request tolerates before it must go next
+constexpr int kMaxBypass = 16;
 
 // Conservative device footprint of one solve: CSR copy + sliced ELLPACK (+ FP32 values for
 // mixed precision) + conversion temporaries + CG work vectors + b and x.
@@ -86,6 +93,17 @@ namespace {
 // duration; they are freed stream-ordered on the slot's stream.
 double since(Clock::time_point t0) {
     return std::chrono::duration<double>(Clock::now() - t0).count();
+}
+
+// The request a free slot admits now (queue end: none): the first in arrival order whose
+// footprint fits the budget's remainder, not passing a request that was passed over
+// kMaxBypass times.  Call with S->mu held.
+std::deque<Request *>::iterator admissible(spmv_server_t S) {
+    for (auto it = S->queue.begin(); it != S->queue.end(); ++it) {
+        if (S->bytes_in_use + (*it)->est_bytes <= S->budget) return it;
+        if ((*it)->bypassed >= kMaxBypass) break;
+    }
+    return S->queue.end();
 }
 
 void run_request(Request *r, cudaStream_t st) {
@@ -152,13 +170,12 @@ void worker(spmv_server_t S) {
         Request *r = nullptr;
         {
             std::unique_lock<std::mutex> lock(S->mu);
-            S->cv.wait(lock, [&] {
-                return S->stop || (!S->queue.empty() &&
-                                   S->bytes_in_use + S->queue.front()->est_bytes <= S->budget);
-            });
+            S->cv.wait(lock, [&] { return S->stop || admissible(S) != S->queue.end(); });
             if (S->stop) break;
-            r = S->queue.front();
-            S->queue.pop_front();
+            auto it = admissible(S);
+            for (auto q = S->queue.begin(); q != it; ++q) (*q)->bypassed += 1;
+            r = *it;
+            S->queue.erase(it);
             S->bytes_in_use += r->est_bytes;
             S->peak = std::max(S->peak, S->bytes_in_use);
             S->active += 1;

@@ -33,6 +33,7 @@ seed gives the same bits on any platform.
 """
 from __future__ import annotations
 
+import os
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -392,6 +393,74 @@ def kuhn_tet_matrix(n, ny=None, nz=None, *, jitter=0.2, seed=0, dirichlet=False,
     m = _build(n, ny, nz, choice, jitter, rng, dirichlet, permute, periodic)
     m.info["kind"] = "kuhn_tet"
     m.info["seed"] = seed
+    return m, rng
+
+
+_FAST_SRC = os.path.join(os.path.dirname(os.path.abspath(__file__)), "kuhnbox.c")
+_fast_lib = None
+
+
+def build_fast(force: bool = False) -> str:
+    """Compile kuhnbox.c (the closed-form Kuhn-box assembler) into lib/libgb300_kuhnbox.so."""
+    import subprocess
+    out_dir = os.path.join(os.path.dirname(_FAST_SRC), "lib")
+    os.makedirs(out_dir, exist_ok=True)
+    path = os.path.join(out_dir, "libgb300_kuhnbox.so")
+    if not force and os.path.exists(path) and os.path.getmtime(path) >= os.path.getmtime(_FAST_SRC):
+        return path
+    tmp = path + ".tmp%d" % os.getpid()
+    subprocess.check_call([os.environ.get("CC", "gcc"), "-O3", "-ffp-contract=off", "-fPIC",
+                           "-shared", "-std=c11", "-o", tmp, _FAST_SRC, "-lm"])
+    os.replace(tmp, path)
+    return path
+
+
+def _fast():
+    global _fast_lib
+    if _fast_lib is None:
+        import ctypes
+        L = ctypes.CDLL(build_fast())
+        L.kuhnbox_assemble.restype = ctypes.c_int
+        L.kuhnbox_assemble.argtypes = [ctypes.c_int64] * 3 + [ctypes.c_void_p] * 2 + [
+            ctypes.c_int] + [ctypes.c_void_p] * 3 + [ctypes.c_int64,
+                                                     ctypes.POINTER(ctypes.c_int64)]
+        _fast_lib = L
+    return _fast_lib
+
+
+def kuhn_tet_matrix_fast(n, ny=None, nz=None, *, jitter=0.2, seed=0, dirichlet=False,
+                         permute=True, rng=None):
+    """The matrix of :func:`kuhn_tet_matrix` (non-periodic boxes), bit for bit, assembled by
+    kuhnbox.c in closed form (no triangle sorting): the same random draws in the same order
+    (vertex jitter, then the cell permutation), then the same element-wise IEEE operations.
+    About ten times faster; ``info`` holds only the box description."""
+    import ctypes
+    ny = n if ny is None else ny
+    nz = n if nz is None else nz
+    rng = np.random.default_rng(seed) if rng is None else rng
+    h = 1.0 / n
+    n_vert = (n + 1) * (ny + 1) * (nz + 1)
+    if jitter > 0.0:
+        jit = np.ascontiguousarray(rng.uniform(-jitter * h, jitter * h, size=(n_vert, 3)))
+    else:
+        jit = np.zeros((n_vert, 3))
+    n_cells = 6 * n * ny * nz
+    perm = rng.permutation(n_cells).astype(np.int64) if permute else None
+    row_ptr = np.empty(n_cells + 1, np.int32)
+    col = np.empty(5 * n_cells, np.int32)
+    val = np.empty(5 * n_cells, np.float64)
+    nnz = ctypes.c_int64()
+    rc = _fast().kuhnbox_assemble(n, ny, nz, jit.ctypes.data,
+                                  perm.ctypes.data if perm is not None else None,
+                                  int(bool(dirichlet)), row_ptr.ctypes.data, col.ctypes.data,
+                                  val.ctypes.data, 5 * n_cells, ctypes.byref(nnz))
+    if rc != 0:
+        raise ValueError("kuhnbox_assemble failed with code %d" % rc)
+    k = int(nnz.value)
+    m = CsrMatrix(n=n_cells, row_ptr=row_ptr, col_idx=col[:k].copy(), values=val[:k].copy(),
+                  perm=perm,
+                  info=dict(nx=n, ny=ny, nz=nz, h=h, jitter=jitter, dirichlet=dirichlet,
+                            periodic=False, kind="kuhn_tet", seed=seed))
     return m, rng
 
 

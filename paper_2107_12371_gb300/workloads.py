@@ -7,6 +7,10 @@ C4  mixed hexahedron / 2-prism / 6-tet mesh, seed 1, Dirichlet, permuted (87^3 ~
 C5  serving stream: independently seeded Kuhn-tet boxes, cell counts log-uniform in
     [1e4, 2e6].
 
+Kuhn-tet boxes of 30^3 hexahedra and more (and every serving request) are assembled by the
+closed-form C assembler meshgen.kuhn_tet_matrix_fast, which gives meshgen.kuhn_tet_matrix's
+matrix bit for bit (tests/test_workloads.py compares the two).
+
 Large matrices are cached as .npz files under ``$GB300_SPMV_CACHE`` (default: the system temp
 directory) keyed by their parameters, so repeated runs skip generation.
 """
@@ -44,8 +48,9 @@ def _cached(key, make):
 def kuhn(n, seed=0, dirichlet=False, jitter=0.2, permute=True, k=None, cache=None):
     """Kuhn-tet n^3 matrix and its U[-1,1] vector (or n x k block) drawn after it."""
     def make():
-        m, rng = meshgen.kuhn_tet_matrix(n, seed=seed, dirichlet=dirichlet, jitter=jitter,
-                                         permute=permute)
+        # the closed-form assembler gives meshgen.kuhn_tet_matrix's matrix bit for bit
+        gen = meshgen.kuhn_tet_matrix_fast if n >= 30 else meshgen.kuhn_tet_matrix
+        m, rng = gen(n, seed=seed, dirichlet=dirichlet, jitter=jitter, permute=permute)
         return m, meshgen.uniform_vectors(rng, m.n, k)
     if cache is None:
         cache = n >= 60
@@ -84,5 +89,5 @@ def serving_request(index, target_cells):
     """Request ``index``: Kuhn-tet box of about ``target_cells`` cells, seed = index,
     Dirichlet, cells permuted, right-hand side U[-1,1]."""
     nx, ny, nz = meshgen.box_for_cells(target_cells)
-    m, rng = meshgen.kuhn_tet_matrix(nx, ny, nz, seed=index, dirichlet=True)
+    m, rng = meshgen.kuhn_tet_matrix_fast(nx, ny, nz, seed=index, dirichlet=True)
     return m, meshgen.uniform_vectors(rng, m.n)

@@ -216,3 +216,42 @@ def test_bad_request_fails_alone(oracle):
     st = capi.spmv_server_get_stats(srv)
     assert st["completed"] == 4 and st["bytes_in_use"] == 0
     capi.spmv_server_destroy(srv)
+
+
+def test_small_request_passes_a_blocked_large_one(oracle):
+    """Admission is by fit, not strictly first-in-first-out: while a long solve holds most of
+    the budget, a queued request too large for the rest waits, and a small request submitted
+    after it is admitted and finishes first; the large one runs once memory frees up."""
+    (ms, bs), (mb, bb) = requests([1e4, 6e4], seed0=300)
+    o = capi.cg_default_options(rtol=1e-8)
+    # the server's footprint estimates, read back as the peak of each request run alone
+    probe = capi.spmv_server_create(8 << 30, 1)
+    est = []
+    for m, b in ((ms, bs), (mb, bb)):
+        t = capi.spmv_server_submit(probe, m.n, m.row_ptr, m.col_idx, m.values, b, o)
+        wait_all(probe, [t], [m])
+        est.append(capi.spmv_server_get_stats(probe)["peak_bytes"])
+    capi.spmv_server_destroy(probe)
+    est_small, est_big = est
+    assert est_big > 2 * est_small
+    # room for one large and one small request, not for two large ones
+    srv = capi.spmv_server_create(est_big + est_small + est_small // 2, 3)
+    endless = capi.cg_default_options(rtol=0.0, max_iter=10 ** 7)
+    t1 = capi.spmv_server_submit(srv, mb.n, mb.row_ptr, mb.col_idx, mb.values, bb, endless)
+    t0 = time.time()
+    while capi.spmv_server_get_stats(srv)["active_slots"] < 1:
+        assert time.time() - t0 < 30.0
+        time.sleep(0.001)
+    t2 = capi.spmv_server_submit(srv, mb.n, mb.row_ptr, mb.col_idx, mb.values, bb, o)
+    t3 = capi.spmv_server_submit(srv, ms.n, ms.row_ptr, ms.col_idx, ms.values, bs, o)
+    x3, r3 = wait_all(srv, [t3], [ms])[0]
+    assert r3["status"] == capi.SPMV_OK and relres(oracle, ms, x3, bs) <= 1e-8
+    # the small one finished while the first large one still runs and the second still waits
+    assert capi.spmv_server_poll(srv, t1, np.empty(mb.n)) is None
+    assert capi.spmv_server_poll(srv, t2, np.empty(mb.n)) is None
+    assert capi.spmv_server_get_stats(srv)["queued"] == 1
+    capi.spmv_server_cancel(srv, t1)
+    (x2, r2), (_, r1) = wait_all(srv, [t2, t1], [mb, mb])
+    assert r1["status"] == capi.SPMV_ERR_CANCELLED
+    assert r2["status"] == capi.SPMV_OK and relres(oracle, mb, x2, bb) <= 1e-8
+    capi.spmv_server_destroy(srv)

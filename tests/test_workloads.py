@@ -43,3 +43,36 @@ def test_serving_request_is_a_dirichlet_kuhn_mesh():
     fwd = sorted(zip(rows.tolist(), m.col_idx.tolist(), m.values.tolist()))
     bwd = sorted(zip(m.col_idx.tolist(), rows.tolist(), m.values.tolist()))
     assert fwd == bwd
+
+
+def test_fast_kuhn_assembler_equals_generator():
+    """The closed-form C assembler used for large boxes and the serving stream gives the
+    generator's matrix bit for bit: same structure, same values, same permutation, same
+    random stream afterwards (cubes and uneven boxes, Neumann and Dirichlet, permuted or not,
+    with and without jitter)."""
+    cases = [(2, 2, 2, 0, True, True, 0.2), (3, 4, 5, 1, False, True, 0.2),
+             (5, 5, 5, 2, True, False, 0.2), (7, 3, 9, 3, True, True, 0.2),
+             (6, 6, 6, 4, False, True, 0.0), (20, 20, 20, 0, False, True, 0.2),
+             (11, 11, 40, 7, True, True, 0.2)]
+    for nx, ny, nz, seed, dirichlet, permute, jitter in cases:
+        ref, r1 = meshgen.kuhn_tet_matrix(nx, ny, nz, seed=seed, dirichlet=dirichlet,
+                                          permute=permute, jitter=jitter)
+        got, r2 = meshgen.kuhn_tet_matrix_fast(nx, ny, nz, seed=seed, dirichlet=dirichlet,
+                                               permute=permute, jitter=jitter)
+        assert got.n == ref.n
+        assert np.array_equal(got.row_ptr, ref.row_ptr)
+        assert np.array_equal(got.col_idx, ref.col_idx)
+        assert np.array_equal(got.values.view(np.uint64), ref.values.view(np.uint64))
+        if permute:
+            assert np.array_equal(got.perm, ref.perm)
+        assert r1.uniform() == r2.uniform()
+
+
+def test_serving_request_uses_the_generator_matrix():
+    """A serving request's matrix is the generator's for its box and seed."""
+    m, b = workloads.serving_request(17, 2.0e4)
+    nx, ny, nz = meshgen.box_for_cells(2.0e4)
+    ref, rng = meshgen.kuhn_tet_matrix(nx, ny, nz, seed=17, dirichlet=True)
+    assert np.array_equal(m.col_idx, ref.col_idx)
+    assert np.array_equal(m.values.view(np.uint64), ref.values.view(np.uint64))
+    assert np.array_equal(b, meshgen.uniform_vectors(rng, ref.n))
