@@ -91,7 +91,24 @@ typedef struct {
     int checks;          /* 1: after the conversion, verify its structures on the device
                           * (spmv_verify) and fail with SPMV_ERR_INVALID_CSR on any violation;
                           * 0 = off (default).  Costs one pass over the matrix at creation. */
+    int spmm_form;       /* kernel form of the multi-vector products whose rows are gathered
+                          * in 32-byte pieces (SPMV_SPMM_*): AUTO = tuned when autotune is on,
+                          * else the measured default.  Every form gives the same bits. */
+    int pq_ctas;         /* CG product grid: CTAs per SM (0 = tuned when autotune is on, else
+                          * 4; 2..4 explicit).  The grid fixes the reduction order of p.q. */
+    int pq_unroll;       /* CG product entries in flight per lane: 0 = tuned / automatic, 2, 5 */
+    int gather_bytes;    /* cg_solve_multi: bytes of a row of P each product lane gathers
+                          * (0 = tuned when autotune is on, else 32; 16 or 32) */
 } spmv_options_t;
+
+/* forms of the 256-bit multi-vector product (spmv_options_t.spmm_form) */
+#define SPMV_SPMM_AUTO 0
+#define SPMV_SPMM_WIDE 1      /* one warp per group of rows, two entries per step          */
+#define SPMV_SPMM_WIDE_PIPE 2 /* the same, the next two entries' values and columns loaded
+                               * while the current rows of X are gathered                   */
+#define SPMV_SPMM_WIDE_GS4 3  /* grid-stride over row blocks, 4 CTAs per SM, the next block's
+                               * matrix data prefetched into L2                              */
+#define SPMV_SPMM_WIDE_GS6 4  /* the same at 6 CTAs per SM                                   */
 
 /* Invariants verified by spmv_verify, one bit each in its result:                      */
 #define SPMV_CHECK_SLICE_PTR 1  /* slice pointers start at 0, grow by multiples of S, end at
@@ -149,6 +166,12 @@ typedef struct {
     size_t device_bytes;     /* device memory owned by the handle                 */
     int32_t index_bits;      /* 32 or 16 (column indices streamed by the kernels) */
     int32_t n_cols;
+    int32_t spmm_form[2][4]; /* SPMV_SPMM_* used by the multi-vector product, per precision
+                              * (0 FP64, 1 FP32) and lanes per row (1, 2, 4, 8: k = 4, 8, 16,
+                              * 32 FP64 or 8, 16, 32, 64 FP32) */
+    int32_t pq_ctas;         /* CG product grid: CTAs per SM                        */
+    int32_t pq_unroll;       /* CG product entries in flight per lane (FP64 handle)  */
+    int32_t gather_bytes;    /* cg_solve_multi product: bytes gathered per lane      */
 } spmv_info_t;
 spmv_status_t spmv_get_info(spmv_matrix_t A, spmv_info_t *info);
 

@@ -32,6 +32,8 @@ SPMV_REORDER_NONE, SPMV_REORDER_RCM, SPMV_REORDER_CM = 0, 1, 2
 SPMV_PREC_FP64, SPMV_PREC_FP32, SPMV_PREC_DUAL = 0, 1, 2
 SPMV_VARIANT_AUTO, SPMV_VARIANT_CSR, SPMV_VARIANT_SELL, SPMV_VARIANT_SELL_WINDOW = 0, 1, 2, 3
 SPMV_VARIANT_SELL_BULK = 4
+SPMV_SPMM_AUTO, SPMV_SPMM_WIDE, SPMV_SPMM_WIDE_PIPE, SPMV_SPMM_WIDE_GS4, SPMV_SPMM_WIDE_GS6 = \
+    0, 1, 2, 3, 4
 
 
 class spmv_options_t(ctypes.Structure):
@@ -40,7 +42,9 @@ class spmv_options_t(ctypes.Structure):
                 ("precision", ctypes.c_int), ("autotune", ctypes.c_int),
                 ("peripheral", ctypes.c_int), ("window_words", ctypes.c_int),
                 ("index_bits", ctypes.c_int), ("sigma", ctypes.c_int),
-                ("checks", ctypes.c_int)]
+                ("checks", ctypes.c_int), ("spmm_form", ctypes.c_int),
+                ("pq_ctas", ctypes.c_int), ("pq_unroll", ctypes.c_int),
+                ("gather_bytes", ctypes.c_int)]
 
 
 class spmv_info_t(ctypes.Structure):
@@ -51,7 +55,9 @@ class spmv_info_t(ctypes.Structure):
                 ("sell_entries", ctypes.c_int64), ("bandwidth", ctypes.c_int32),
                 ("max_slice_span", ctypes.c_int32), ("window_words", ctypes.c_int32),
                 ("device_bytes", ctypes.c_size_t), ("index_bits", ctypes.c_int32),
-                ("n_cols", ctypes.c_int32)]
+                ("n_cols", ctypes.c_int32), ("spmm_form", (ctypes.c_int32 * 4) * 2),
+                ("pq_ctas", ctypes.c_int32), ("pq_unroll", ctypes.c_int32),
+                ("gather_bytes", ctypes.c_int32)]
 
 
 class cg_options_t(ctypes.Structure):
@@ -233,7 +239,11 @@ def spmv_destroy(h):
 def spmv_get_info(h):
     info = spmv_info_t()
     _check(load().spmv_get_info(h, ctypes.byref(info)), "spmv_get_info")
-    return {f: getattr(info, f) for f, _ in spmv_info_t._fields_}
+    out = {}
+    for f, _ in spmv_info_t._fields_:
+        v = getattr(info, f)
+        out[f] = [list(r) for r in v] if f == "spmm_form" else v
+    return out
 
 
 def spmv_verify(h, stream=None):

@@ -59,6 +59,12 @@ static spmv_status_t normalize_options(const spmv_options_t *in, spmv_options_t 
     if (o->sigma != 0 && (o->sigma < 32 || o->sigma > 4096 || (o->sigma & (o->sigma - 1)) != 0))
         return SPMV_ERR_INVALID_ARG;
     if (o->checks != 0 && o->checks != 1) return SPMV_ERR_INVALID_ARG;
+    if (o->spmm_form < SPMV_SPMM_AUTO || o->spmm_form > SPMV_SPMM_WIDE_GS6)
+        return SPMV_ERR_INVALID_ARG;
+    if (o->pq_ctas != 0 && (o->pq_ctas < 2 || o->pq_ctas > 4)) return SPMV_ERR_INVALID_ARG;
+    if (o->pq_unroll != 0 && o->pq_unroll != 2 && o->pq_unroll != 5) return SPMV_ERR_INVALID_ARG;
+    if (o->gather_bytes != 0 && o->gather_bytes != 16 && o->gather_bytes != 32)
+        return SPMV_ERR_INVALID_ARG;
     return SPMV_OK;
 }
 
@@ -133,6 +139,9 @@ spmv_status_t spmv_create(int32_t n_rows, int32_t n_cols, int64_t nnz, const int
     A->opt = o;
     A->S = o.slice_height;
     A->block = o.block;
+    A->pq_ctas = o.pq_ctas;
+    A->pq_unroll = o.pq_unroll;
+    A->mcg_bytes = o.gather_bytes ? o.gather_bytes : 32;
 
     int32_t *d_rp = nullptr, *d_ci = nullptr;
     double *d_val = nullptr;
@@ -250,6 +259,11 @@ spmv_status_t spmv_get_info(spmv_matrix_t A, spmv_info_t *info) {
     info->window_words = A->window_words;
     info->device_bytes = A->bytes;
     info->index_bits = A->index_bits;
+    for (int p = 0; p < 2; ++p)
+        for (int g = 0; g < 4; ++g) info->spmm_form[p][g] = spmm_form_of(A, p == 1, g);
+    info->pq_ctas = A->pq_ctas;
+    info->pq_unroll = A->pq_unroll;
+    info->gather_bytes = A->mcg_bytes;
     return SPMV_OK;
 }
 
@@ -350,6 +364,8 @@ spmv_status_t spmv_apply_multi(spmv_matrix_t A, int k, const double *X, double *
     if (A->n > 0 && (!X || !Y || X == Y || !aligned16(X) || !aligned16(Y)))
         return SPMV_ERR_INVALID_ARG;
     if (!A->has64()) return SPMV_ERR_UNSUPPORTED;
+    if (A->opt.autotune && A->opt.spmm_form == SPMV_SPMM_AUTO)
+        GB_TRY(tune_spmm64(A, k, X, Y, (cudaStream_t)stream));
     return launch_spmm64(A, k, X, Y, (cudaStream_t)stream);
 }
 
@@ -359,6 +375,8 @@ spmv_status_t spmv_apply_multi_f32(spmv_matrix_t A, int k, const float *X, float
     if (A->n > 0 && (!X || !Y || X == Y || !aligned16(X) || !aligned16(Y)))
         return SPMV_ERR_INVALID_ARG;
     if (!A->has32()) return SPMV_ERR_UNSUPPORTED;
+    if (A->opt.autotune && A->opt.spmm_form == SPMV_SPMM_AUTO)
+        GB_TRY(tune_spmm32(A, k, X, Y, (cudaStream_t)stream));
     return launch_spmm32(A, k, X, Y, (cudaStream_t)stream);
 }
 

@@ -12,6 +12,7 @@
 // scalars the next kernel reads.  Results therefore do not depend on CTA scheduling.  A
 // "done" flag set by that last CTA turns the remaining kernels of a CUDA-graph batch into
 // no-ops, so the host only checks convergence once per batch of iterations.
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -239,26 +240,39 @@ __global__ void add_iters(CgScalars *inner, int *total) { *total += inner->iters
 
 }  // namespace
 
-// Grid of the CG sweeps of a matrix with n rows: about 1,024 rows (4 per thread) per CTA, at
-// most kCgCtasPerSm CTAs per SM (the persistent kernel uses the same grid).  It depends only
-// on n and the device, so the reduction order is fixed per handle and both paths give
-// identical results; small systems use fewer CTAs and leave room for concurrent solves.
-int cg_pq_grid(int32_t n_slices, int L, int value_bytes) {
-    const int64_t cap = (int64_t)device_facts().sm_count * pq_min_ctas(value_bytes);
-    const int64_t want = ((int64_t)n_slices * L + kCgBlock - 1) / kCgBlock;
+// Grid of the CG product q = A p: one thread per slice-lane, at most the handle's pq_ctas CTAs
+// per SM (tuned, or set by option; default pq_min_ctas).  The grid fixes the order of the p.q
+// reduction, so it is a property of the handle, shared by the graph path and the persistent
+// kernel (which runs it as virtual CTAs): both give identical results.
+int cg_pq_grid(const spmv_matrix_t A, int L, int value_bytes) {
+    const int per_sm = A->pq_ctas > 0 ? A->pq_ctas : pq_min_ctas(value_bytes);
+    const int64_t cap = (int64_t)device_facts().sm_count * per_sm;
+    const int64_t want = ((int64_t)A->n_slices * L + kCgBlock - 1) / kCgBlock;
     return (int)(want < 1 ? 1 : (want > cap ? cap : want));
+}
+
+// Entries the product keeps in flight per lane: the handle's pq_unroll (tuned, or set by
+// option), else five when the widest slice then needs fewer dependent load rounds than with
+// two (the per-row order, hence the result, is the same either way).
+bool cg_pq_deep(const spmv_matrix_t A, int uu) {
+    if (A->pq_unroll > 0) return A->pq_unroll > 2;
+    return load_rounds(A->max_width, uu) < load_rounds(A->max_width, 2);
 }
 
 // (lanes per slice, value bytes per lane entry) of the FP64 and FP32 product kernels for a
 // slice height, as with_shape picks them
 static int pq_grid64(const spmv_matrix_t A) {
-    return cg_pq_grid(A->n_slices, 32, 8 * (A->S / 32));
+    return cg_pq_grid(A, 32, 8 * (A->S / 32));
 }
 static int pq_grid32(const spmv_matrix_t A) {
     const int L = A->S / 4 < 32 ? A->S / 4 : 32;
-    return cg_pq_grid(A->n_slices, L, 4 * (A->S / L));
+    return cg_pq_grid(A, L, 4 * (A->S / L));
 }
 
+// Grid of the CG sweeps of a matrix with n rows: about 1,024 rows (4 per thread) per CTA, at
+// most kCgCtasPerSm CTAs per SM (the persistent kernel uses the same grid).  It depends only
+// on n and the device, so the reduction order is fixed per handle and both paths give
+// identical results; small systems use fewer CTAs and leave room for concurrent solves.
 int cg_grid(int32_t n) {
     const int cap = device_facts().sm_count * kCgCtasPerSm;
     const int64_t want = ((int64_t)n + 1023) / 1024;
@@ -272,10 +286,9 @@ spmv_status_t ensure_cg_work(spmv_matrix_t A, bool mixed, cudaStream_t st) {
     if (!w.ready) {
         const int G = cg_grid(A->n);
         w.part_len = G;
-        // the product's p.q partials (the larger of its FP64 and FP32 grids), then
+        // the product's p.q partials (room for the largest grid any pq_ctas gives), then
         // kMaxParts partials per CTA of the sweeps
-        const int g64 = pq_grid64(A), g32 = pq_grid32(A);
-        w.pq_len = g64 > g32 ? g64 : g32;
+        w.pq_len = device_facts().sm_count * 4;
         GB_TRY(w.part.alloc((size_t)w.pq_len + (size_t)G * kMaxParts * 2, t));
         GB_TRY(w.scal.alloc(2 * ((sizeof(CgScalars) + 7) / 8), t));
         GB_CUDA(cudaMemsetAsync(w.scal.p, 0, w.scal.n * sizeof(double), st));
@@ -330,7 +343,7 @@ static spmv_status_t enqueue_cg64(spmv_matrix_t A, int iters, cudaStream_t st) {
             constexpr int R = decltype(rt)::value, L = decltype(lt)::value;
             const int Gpq = pq_grid64(A);
             constexpr int UU = pq_unroll(8 * R);
-            const bool deep = load_rounds(A->max_width, UU) < load_rounds(A->max_width, 2);
+            const bool deep = cg_pq_deep(A, UU);
             for (int it = 0; it < iters; ++it) {
                 if (deep)
                     cg_spmv_pq<double, R, L, ColT, UU><<<Gpq, kCgBlock, 0, st>>>(
@@ -350,6 +363,89 @@ static spmv_status_t enqueue_cg64(spmv_matrix_t A, int iters, cudaStream_t st) {
     });
 }
 
+__global__ void fill_value(int32_t n, double *v, double value) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        v[i] = value;
+}
+
+// one FP64 product q = A p with p.q (the first kernel of an iteration), on scalar block sc
+static spmv_status_t enqueue_pq64(spmv_matrix_t A, CgScalars *sc, cudaStream_t st) {
+    CgWork &w = A->cg;
+    return with_cols(A, [&](auto cols) -> spmv_status_t {
+        using ColT = decltype(cols);
+        return with_shape(A->S, false, [&](auto rt, auto lt) -> spmv_status_t {
+            constexpr int R = decltype(rt)::value, L = decltype(lt)::value;
+            constexpr int UU = pq_unroll(8 * R);
+            if (cg_pq_deep(A, UU))
+                cg_spmv_pq<double, R, L, ColT, UU><<<pq_grid64(A), kCgBlock, 0, st>>>(
+                    A->n, A->n_slices, A->slice_ptr.p, cols, A->sell_val.p, w.p.p, w.q.p,
+                    w.part.p, sc);
+            else
+                cg_spmv_pq<double, R, L, ColT, 2><<<pq_grid64(A), kCgBlock, 0, st>>>(
+                    A->n, A->n_slices, A->slice_ptr.p, cols, A->sell_val.p, w.p.p, w.q.p,
+                    w.part.p, sc);
+            GB_LAUNCHED();
+            return SPMV_OK;
+        });
+    });
+}
+
+// Tuner of the CG product: its grid (2, 3 or 4 CTAs per SM) and the entries each lane keeps in
+// flight (2 or 5).  Each candidate computes q = A p with p = 1 (the gathers and multiply-adds
+// of a solve; the scalars go to the inner block, which every solve resets before use), timed
+// as the median of three launches each after writing a buffer of twice the L2 size, as in
+// steady use; the fastest is kept.  The FP32 product of a refinement uses the same grid.  The
+// choice fixes the handle's p.q reduction order for every later solve, on both paths.
+static spmv_status_t tune_cg_product(spmv_matrix_t A, cudaStream_t st) {
+    A->pq_tuned = true;
+    if (A->opt.pq_ctas || A->opt.pq_unroll) return SPMV_OK;
+    CgWork &w = A->cg;
+    CgScalars *sc = inner_scalars(A);
+    fill_value<<<(unsigned)std::min<int64_t>(((int64_t)A->n + 255) / 256, 4096), 256, 0, st>>>(
+        A->n, w.p.p, 1.0);
+    GB_LAUNCHED();
+    const size_t fb = 2 * (size_t)(device_facts().l2_bytes > 0 ? device_facts().l2_bytes
+                                                               : (128 << 20));
+    void *flush = nullptr;
+    GB_CUDA(gb_malloc_async(&flush, fb, st));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    spmv_status_t s = cuda_status(cudaEventCreate(&e0));
+    if (s == SPMV_OK) s = cuda_status(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_ctas = 0, best_uu = 0;
+    for (int ctas = 2; ctas <= 4 && s == SPMV_OK; ++ctas) {
+        for (int uu : {2, 5}) {
+            A->pq_ctas = ctas;
+            A->pq_unroll = uu;
+            float t[3] = {0.f, 0.f, 0.f};
+            for (int i = -1; i < 3 && s == SPMV_OK; ++i) {  // i = -1: warm-up
+                set_scalars<<<1, 1, 0, st>>>(sc, 0.0, 1);
+                s = cuda_status(cudaGetLastError());
+                if (s == SPMV_OK) s = cuda_status(cudaMemsetAsync(flush, i + 2, fb, st));
+                if (s == SPMV_OK) s = cuda_status(cudaEventRecord(e0, st));
+                if (s == SPMV_OK) s = enqueue_pq64(A, sc, st);
+                if (s == SPMV_OK) s = cuda_status(cudaEventRecord(e1, st));
+                if (s == SPMV_OK) s = cuda_status(cudaEventSynchronize(e1));
+                if (s == SPMV_OK && i >= 0) s = cuda_status(cudaEventElapsedTime(&t[i], e0, e1));
+            }
+            if (s != SPMV_OK) break;
+            const float med = std::max(std::min(t[0], t[1]), std::min(std::max(t[0], t[1]), t[2]));
+            if (med < best) {
+                best = med;
+                best_ctas = ctas;
+                best_uu = uu;
+            }
+        }
+    }
+    A->pq_ctas = s == SPMV_OK ? best_ctas : 0;
+    A->pq_unroll = s == SPMV_OK ? best_uu : 0;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFreeAsync(flush, st);
+    return s;
+}
+
 static spmv_status_t enqueue_cg32(spmv_matrix_t A, int iters, cudaStream_t st) {
     CgWork &w = A->cg;
     const int G = cg_grid(A->n);
@@ -360,7 +456,7 @@ static spmv_status_t enqueue_cg32(spmv_matrix_t A, int iters, cudaStream_t st) {
             constexpr int R = decltype(rt)::value, L = decltype(lt)::value;
             const int Gpq = pq_grid32(A);
             constexpr int UU = pq_unroll(4 * R);
-            const bool deep = load_rounds(A->max_width, UU) < load_rounds(A->max_width, 2);
+            const bool deep = cg_pq_deep(A, UU);
             for (int it = 0; it < iters; ++it) {
                 if (deep)
                     cg_spmv_pq<float, R, L, ColT, UU><<<Gpq, kCgBlock, 0, st>>>(
@@ -719,6 +815,10 @@ spmv_status_t gb::cg_solve_ex(spmv_matrix_t A, const double *b, double *x,
     const auto t0 = Clock::now();
     spmv_status_t s = ensure_cg_work(A, o.mixed != 0, st);
     if (s != SPMV_OK) return (res->status = s);
+    if (A->opt.autotune && !A->pq_tuned) {
+        s = tune_cg_product(A, st);
+        if (s != SPMV_OK) return (res->status = s);
+    }
     CgWork &w = A->cg;
     if (o.use_x0)
         s = cuda_status(cudaMemcpyAsync(w.x.p, x, sizeof(double) * A->n, cudaMemcpyDeviceToDevice, st));

@@ -25,7 +25,8 @@ int cg_grid(int32_t n);
 // both paths stay bit-identical.
 constexpr int pq_min_ctas(int value_bytes) { return value_bytes >= 64 ? 3 : 4; }
 constexpr int pq_unroll(int value_bytes) { return value_bytes <= 16 ? 5 : 2; }
-int cg_pq_grid(int32_t n_slices, int L, int value_bytes);
+int cg_pq_grid(const spmv_matrix_t A, int L, int value_bytes);
+bool cg_pq_deep(const spmv_matrix_t A, int uu);
 
 // Hint: bring the line holding p into L1 without waiting for it (a later load of it hits).
 __device__ __forceinline__ void prefetch_l1(const void *p) {

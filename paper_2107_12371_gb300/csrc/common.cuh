@@ -176,6 +176,13 @@ struct spmv_matrix_s {
     gb::CgWork cg;
     gb::McgWork *mcg = nullptr;  // created by the first cg_solve_multi
     int mcg_bytes = 32;          // cg_solve_multi: bytes of a row each product lane gathers
+    bool mcg_tuned = false;      // mcg_bytes chosen by the tuner
+    int pq_ctas = 0;             // CG product grid: CTAs per SM (0: pq_min_ctas)
+    int pq_unroll = 0;           // CG product entries in flight (0: by load rounds)
+    bool pq_tuned = false;       // pq_ctas / pq_unroll chosen by the tuner
+    // SpMM form per precision (0 FP64, 1 FP32) and lanes per row (1, 2, 4, 8) chosen by the
+    // tuner on the first multi-vector product of that shape (SPMV_SPMM_AUTO: not tuned)
+    int spmm_tuned[2][4] = {};
 
     // spmv_apply_host(_async): two staging sets used in turn, each with device copies of x and
     // y, two streams of its own (product, device-to-host) and events; created on first use
@@ -212,6 +219,9 @@ spmv_status_t launch_spmv32(spmv_matrix_t A, const float *x, float *y, cudaStrea
 spmv_status_t launch_spmv_csr64(spmv_matrix_t A, const double *x, double *y, cudaStream_t st);
 spmv_status_t launch_spmm64(spmv_matrix_t A, int k, const double *X, double *Y, cudaStream_t st);
 spmv_status_t launch_spmm32(spmv_matrix_t A, int k, const float *X, float *Y, cudaStream_t st);
+spmv_status_t tune_spmm64(spmv_matrix_t A, int k, const double *X, double *Y, cudaStream_t st);
+spmv_status_t tune_spmm32(spmv_matrix_t A, int k, const float *X, float *Y, cudaStream_t st);
+int spmm_form_of(const spmv_matrix_t A, bool f32, int gi);
 spmv_status_t launch_permute(spmv_matrix_t A, int direction, int elem_bytes, const void *in,
                              void *out, cudaStream_t st);
 int window_capacity_words(int elem_bytes);

@@ -20,6 +20,7 @@
 // With opt->mixed the same kernels run in FP32 as the inner solves of FP64 iterative
 // refinement (per column: FP64 residual, FP32 inner Jacobi-PCG on r_c / ||r_c|| to the inner
 // tolerance of the single-RHS refinement, FP64 update x_c += ||r_c|| d_c).
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <mutex>
@@ -927,6 +928,79 @@ spmv_status_t enqueue_iters(spmv_matrix_t A, bool f32, int iters, int bytes, cud
     return run(double{});
 }
 
+// every column running (for timing the product outside a solve)
+__global__ void mcg_activate(McgScalars *sc, int kp) {
+    const int c = threadIdx.x;
+    if (c < kp) {
+        sc->col[c].done = 0;
+        sc->col[c].rho = 1.0;
+    }
+    if (c == 0) {
+        sc->active = kp;
+        sc->pending = 0;
+        for (int t = 0; t < 4; ++t) sc->tickets[t] = 0u;
+    }
+}
+
+// Tuner of the FP64 product's gather width (32- or 16-byte pieces of a row of P per lane):
+// each width computes Q = A P for P = the packed right-hand sides, timed as the median of
+// three launches each after writing a buffer of twice the L2 size; the faster is kept for
+// the handle.  The width fixes the p.q reduction order of the handle's later multi-RHS solves.
+spmv_status_t tune_gather(spmv_matrix_t A, cudaStream_t st) {
+    A->mcg_tuned = true;
+    if (A->opt.gather_bytes) return SPMV_OK;
+    McgWork &w = *A->mcg;
+    McgScalars *sc = block_of(A, 1);
+    GB_CUDA(cudaMemcpyAsync(w.P.p, w.B.p, sizeof(double) * (size_t)A->n * w.kp,
+                            cudaMemcpyDeviceToDevice, st));
+    const size_t fb = 2 * (size_t)(device_facts().l2_bytes > 0 ? device_facts().l2_bytes
+                                                               : (128 << 20));
+    void *flush = nullptr;
+    GB_CUDA(gb_malloc_async(&flush, fb, st));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    spmv_status_t s = cuda_status(cudaEventCreate(&e0));
+    if (s == SPMV_OK) s = cuda_status(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_bytes = 32;
+    for (int bytes : {32, 16}) {
+        float t[3] = {0.f, 0.f, 0.f};
+        for (int i = -1; i < 3 && s == SPMV_OK; ++i) {  // i = -1: warm-up
+            mcg_activate<<<1, kMcgMaxCols, 0, st>>>(sc, w.kp);
+            s = cuda_status(cudaGetLastError());
+            if (s == SPMV_OK) s = cuda_status(cudaMemsetAsync(flush, i + 2, fb, st));
+            if (s == SPMV_OK) s = cuda_status(cudaEventRecord(e0, st));
+            if (s == SPMV_OK)
+                s = with_mcg_cols(A, [&](auto cols) -> spmv_status_t {
+                    using ColT = decltype(cols);
+                    return with_piece<double>(w.kp, bytes, [&](auto gt, auto bt) -> spmv_status_t {
+                        constexpr int G = decltype(gt)::value, BY = decltype(bt)::value;
+                        mcg_product<double, G, BY, ColT><<<product_grid(A, G, 8), kCgBlock, 0,
+                                                           st>>>(A->n, A->S, A->n_slices,
+                                                                 A->slice_ptr.p, cols,
+                                                                 A->sell_val.p, w.P.p, w.Q.p,
+                                                                 w.part.p, sc);
+                        GB_LAUNCHED();
+                        return SPMV_OK;
+                    });
+                });
+            if (s == SPMV_OK) s = cuda_status(cudaEventRecord(e1, st));
+            if (s == SPMV_OK) s = cuda_status(cudaEventSynchronize(e1));
+            if (s == SPMV_OK && i >= 0) s = cuda_status(cudaEventElapsedTime(&t[i], e0, e1));
+        }
+        if (s != SPMV_OK) break;
+        const float med = std::max(std::min(t[0], t[1]), std::min(std::max(t[0], t[1]), t[2]));
+        if (med < best) {
+            best = med;
+            best_bytes = bytes;
+        }
+    }
+    if (s == SPMV_OK) A->mcg_bytes = best_bytes;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFreeAsync(flush, st);
+    return s;
+}
+
 spmv_status_t enqueue_residual(spmv_matrix_t A, bool x_zero, bool want_p, int mode,
                                cudaStream_t st) {
     McgWork &w = *A->mcg;
@@ -1264,12 +1338,16 @@ extern "C" spmv_status_t cg_solve_multi(spmv_matrix_t A, int k, const double *B,
     s = ensure_mcg_work(A, kp, o.mixed != 0, st);
     if (s != SPMV_OK) return fail(s);
     McgWork &w = *A->mcg;
-    const int bytes = A->mcg_bytes == 16 ? 16 : 32;
     const unsigned pg = pack_grid((int64_t)A->n * kp);
     mcg_pack<double><<<pg, 256, 0, st>>>(A->n, k, kp, B, w.B.p);
     mcg_pack<double><<<pg, 256, 0, st>>>(A->n, k, kp, o.use_x0 ? X : nullptr, w.X.p);
     s = cuda_status(cudaGetLastError());
     if (s != SPMV_OK) return fail(s);
+    if (A->opt.autotune && !A->mcg_tuned) {
+        s = tune_gather(A, st);
+        if (s != SPMV_OK) return fail(s);
+    }
+    const int bytes = A->mcg_bytes == 16 ? 16 : 32;
     spmv_status_t col_status[kMcgMaxCols];
     for (int c = 0; c < k; ++c) col_status[c] = SPMV_OK;
     int outer = 0;

@@ -245,10 +245,10 @@ static spmv_status_t run_persistent(spmv_matrix_t A, bool f32, const cg_options_
             }
             double *part = w.part.p;
             // the graph path's product grid for this shape (see cg_pq_grid)
-            int32_t Gpq = cg_pq_grid(A->n_slices, L, (int)sizeof(T) * R);
+            int32_t Gpq = cg_pq_grid(A, L, (int)sizeof(T) * R);
             int32_t pq_len = w.pq_len;
             constexpr int UU = pq_unroll((int)sizeof(T) * R);
-            int deep = load_rounds(A->max_width, UU) < load_rounds(A->max_width, 2) ? 1 : 0;
+            int deep = cg_pq_deep(A, UU) ? 1 : 0;
             void *args[] = {&n, &ns, &sp, &cols, &val, &x, &r, &p, &q, &dinv, &part, &Gpq,
                             &pq_len, &deep, &sc};
             GB_CUDA(cudaLaunchCooperativeKernel((const void *)kern, dim3(w.pers_grid),

@@ -4,6 +4,7 @@
 // every gathered row of X (k contiguous values) is read once per matrix entry and used for
 // all k columns.  Column c of Y equals the single-vector product of column c bit for bit
 // (same entry order, fused multiply-add from +0.0).
+#include <algorithm>
 #include <type_traits>
 
 #include "common.cuh"
@@ -377,6 +378,121 @@ spmm_sell_wide_pipe(int32_t n, int32_t S, int32_t n_slices, const int64_t *__res
     if (row < n) Wide<T>::store(Y + row * K + g * VW, acc);
 }
 
+// The rows of one warp (RPW = 32 / G rows from row0, inside one slice) of the 256-bit SpMM:
+// the body of spmm_sell_wide, two entries per step.
+template <typename T, int G, typename ColT>
+__device__ __forceinline__ void wide_warp_rows(int64_t row0, int32_t n, int32_t S,
+                                               const int64_t *__restrict__ sp, ColT cols,
+                                               const T *__restrict__ val,
+                                               const T *__restrict__ X, T *__restrict__ Y,
+                                               uint64_t pol) {
+    constexpr int VW = Wide<T>::n;
+    constexpr int K = VW * G;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane / G, g = lane % G;
+    const int64_t row = row0 + sub;
+    const int64_t slice = row0 / S;
+    const int64_t r = row - slice * S;
+    const int64_t base = sp[slice];
+    const int w = (int)((sp[slice + 1] - base) / S);
+    const int32_t cbase = cols.base(slice);
+    const T *vp = val + base + r;
+    const int64_t cat = base + r;
+    const T *xg = X + g * VW;
+    T acc[VW];
+#pragma unroll
+    for (int j = 0; j < VW; ++j) acc[j] = T(0);
+    int t = 0;
+    for (; t + 2 <= w; t += 2) {
+        T a[2][1];
+        int32_t c[2][1];
+        ld_stream(vp + (int64_t)t * S, pol, a[0]);
+        cols.template load<1>(cat + (int64_t)t * S, slice, pol, cbase, c[0]);
+        ld_stream(vp + (int64_t)(t + 1) * S, pol, a[1]);
+        cols.template load<1>(cat + (int64_t)(t + 1) * S, slice, pol, cbase, c[1]);
+        T xv[2][VW];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            if (c[u][0] >= 0) Wide<T>::load(xg + (int64_t)c[u][0] * K, xv[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+            if (c[u][0] >= 0) {
+#pragma unroll
+                for (int j = 0; j < VW; ++j) acc[j] = fma_t(a[u][0], xv[u][j], acc[j]);
+            }
+    }
+    if (t < w) {
+        T a[1];
+        int32_t c[1];
+        ld_stream(vp + (int64_t)t * S, pol, a);
+        cols.template load<1>(cat + (int64_t)t * S, slice, pol, cbase, c);
+        if (c[0] >= 0) {
+            T xv[VW];
+            Wide<T>::load(xg + (int64_t)c[0] * K, xv);
+#pragma unroll
+            for (int j = 0; j < VW; ++j) acc[j] = fma_t(a[0], xv[j], acc[j]);
+        }
+    }
+    if (row < n) Wide<T>::store(Y + row * K + g * VW, acc);
+}
+
+// L2 prefetch of the matrix data (values and column indices) of the slices holding rows
+// [rlo, rhi): one 128-byte line per lane of the calling warp.
+template <typename T, typename ColT>
+__device__ __forceinline__ void prefetch_rows_l2(int64_t rlo, int64_t rhi, int32_t S,
+                                                 const int64_t *sp, ColT cols, const T *val) {
+    const int lane = threadIdx.x & 31;
+    const int64_t e0 = sp[rlo / S], e1 = sp[(rhi + S - 1) / S];
+    const uintptr_t v0 = (uintptr_t)(val + e0) & ~(uintptr_t)127;
+    const uintptr_t v1 = (uintptr_t)(val + e1);
+    for (uintptr_t p = v0 + 128 * (uintptr_t)lane; p < v1; p += 128 * 32)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+    const uintptr_t c0 = (uintptr_t)(cols.col + e0) & ~(uintptr_t)127;
+    const uintptr_t c1 = (uintptr_t)(cols.col + e1);
+    for (uintptr_t p = c0 + 128 * (uintptr_t)lane; p < c1; p += 128 * 32)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// The 256-bit SpMM as a grid-stride loop over blocks of 8 RPW rows (one per CTA step) on a
+// grid of MINB CTAs per SM, warp 0 prefetching into L2 the matrix data of the block the CTA
+// takes next, so that the (value, column) loads of the next block hit L2 instead of waiting on
+// DRAM before their gathers can start.  Same per-row order, hence the same bits.
+template <typename T, int G, int MINB, typename ColT>
+__global__ void __launch_bounds__(256, MINB)
+spmm_sell_wide_gs(int32_t n, int32_t S, int32_t n_slices, const int64_t *__restrict__ sp,
+                  ColT cols, const T *__restrict__ val, const T *__restrict__ X,
+                  T *__restrict__ Y) {
+    constexpr int RPW = 32 / G;
+    constexpr int64_t RB = 8 * RPW;
+    const int warp = threadIdx.x >> 5;
+    const int64_t rows_total = (int64_t)n_slices * S;
+    const int64_t nblocks = (rows_total + RB - 1) / RB;
+    const uint64_t pol = policy_evict_first();
+    for (int64_t blk = blockIdx.x; blk < nblocks; blk += gridDim.x) {
+        const int64_t nxt = blk + gridDim.x;
+        if (warp == 0 && nxt < nblocks)
+            prefetch_rows_l2(nxt * RB, nxt * RB + RB < rows_total ? nxt * RB + RB : rows_total,
+                             S, sp, cols, val);
+        const int64_t row0 = blk * RB + (int64_t)warp * RPW;
+        if (row0 < rows_total) wide_warp_rows<T, G>(row0, n, S, sp, cols, val, X, Y, pol);
+    }
+}
+
+}  // namespace
+
+// Kernel form of the 256-bit SpMM for a handle, precision and lanes-per-row class: the
+// handle's choice (option or tuner), else the measured default (the software-pipelined form
+// for FP32 rows of one lane, the plain form otherwise).
+int spmm_form_of(const spmv_matrix_t A, bool f32, int gi) {
+    if (A->opt.spmm_form != SPMV_SPMM_AUTO) return A->opt.spmm_form;
+    const int t = A->spmm_tuned[f32 ? 1 : 0][gi];
+    if (t != SPMV_SPMM_AUTO) return t;
+    return (f32 && gi == 0) ? SPMV_SPMM_WIDE_PIPE : SPMV_SPMM_WIDE;
+}
+
+namespace {
+
 template <typename T>
 spmv_status_t launch_spmm(spmv_matrix_t A, int k, const T *val, const T *X, T *Y,
                           cudaStream_t st) {
@@ -388,28 +504,35 @@ spmv_status_t launch_spmm(spmv_matrix_t A, int k, const T *val, const T *X, T *Y
     const bool al32 = ((uintptr_t)X % 32 == 0) && ((uintptr_t)Y % 32 == 0);
     auto wide = [&](auto gtag) -> spmv_status_t {
         constexpr int G = decltype(gtag)::value;
+        constexpr int gi = G == 1 ? 0 : (G == 2 ? 1 : (G == 4 ? 2 : 3));
         const int64_t warps = (rows_total + (32 / G) - 1) / (32 / G);
         const unsigned grid = grid_for(warps * 32, block);
-        constexpr bool pipe = sizeof(T) == 4 && G == 1;
-        if (A->index_bits == 16) {
-            const Cols16 c16{A->sell_col16.p, A->col_start.p};
-            if constexpr (pipe)
-                spmm_sell_wide_pipe<T, G, Cols16><<<grid, block, 0, st>>>(
-                    A->n, A->S, A->n_slices, A->slice_ptr.p, c16, val, X, Y);
-            else
-                spmm_sell_wide<T, G, Cols16><<<grid, block, 0, st>>>(
-                    A->n, A->S, A->n_slices, A->slice_ptr.p, c16, val, X, Y);
-        } else {
-            const Cols32 c32{A->sell_col.p};
-            if constexpr (pipe)
-                spmm_sell_wide_pipe<T, G, Cols32><<<grid, block, 0, st>>>(
-                    A->n, A->S, A->n_slices, A->slice_ptr.p, c32, val, X, Y);
-            else
-                spmm_sell_wide<T, G, Cols32><<<grid, block, 0, st>>>(
-                    A->n, A->S, A->n_slices, A->slice_ptr.p, c32, val, X, Y);
-        }
-        GB_LAUNCHED();
-        return SPMV_OK;
+        const int sms = device_facts().sm_count;
+        const int form = spmm_form_of(A, sizeof(T) == 4, gi);
+        auto go = [&](auto cols) -> spmv_status_t {
+            using ColT = decltype(cols);
+            switch (form) {
+                case SPMV_SPMM_WIDE_PIPE:
+                    spmm_sell_wide_pipe<T, G, ColT><<<grid, block, 0, st>>>(
+                        A->n, A->S, A->n_slices, A->slice_ptr.p, cols, val, X, Y);
+                    break;
+                case SPMV_SPMM_WIDE_GS4:
+                    spmm_sell_wide_gs<T, G, 4, ColT><<<sms * 4, block, 0, st>>>(
+                        A->n, A->S, A->n_slices, A->slice_ptr.p, cols, val, X, Y);
+                    break;
+                case SPMV_SPMM_WIDE_GS6:
+                    spmm_sell_wide_gs<T, G, 6, ColT><<<sms * 6, block, 0, st>>>(
+                        A->n, A->S, A->n_slices, A->slice_ptr.p, cols, val, X, Y);
+                    break;
+                default:
+                    spmm_sell_wide<T, G, ColT><<<grid, block, 0, st>>>(
+                        A->n, A->S, A->n_slices, A->slice_ptr.p, cols, val, X, Y);
+            }
+            GB_LAUNCHED();
+            return SPMV_OK;
+        };
+        if (A->index_bits == 16) return go(Cols16{A->sell_col16.p, A->col_start.p});
+        return go(Cols32{A->sell_col.p});
     };
     if (al32) {
         using std::integral_constant;
@@ -471,7 +594,66 @@ spmv_status_t launch_spmm(spmv_matrix_t A, int k, const T *val, const T *X, T *Y
     return go(I32{}, I2{});
 }
 
+// Tuner of the 256-bit SpMM's form for this (precision, k): each form in turn computes the
+// caller's product (warm-up launch, then the median of three launches, each after writing a
+// buffer of twice the L2 size so that the matrix and X come from DRAM as in steady use); the
+// fastest is kept for the handle.  The product left in Y is the last form's, and every form
+// gives the same bits.
+template <typename T>
+spmv_status_t tune_spmm(spmv_matrix_t A, int k, const T *val, const T *X, T *Y,
+                        cudaStream_t st) {
+    constexpr int WV = Wide<T>::n;
+    const bool al32 = ((uintptr_t)X % 32 == 0) && ((uintptr_t)Y % 32 == 0);
+    int gi = -1;
+    for (int g = 0, G = 1; g < 4; ++g, G *= 2)
+        if (k == WV * G) gi = g;
+    if (!al32 || gi < 0 || A->n == 0) return SPMV_OK;
+    int &slot = A->spmm_tuned[sizeof(T) == 4 ? 1 : 0][gi];
+    if (slot != SPMV_SPMM_AUTO) return SPMV_OK;
+    const size_t fb = 2 * (size_t)(device_facts().l2_bytes > 0 ? device_facts().l2_bytes
+                                                               : (128 << 20));
+    void *flush = nullptr;
+    GB_CUDA(gb_malloc_async(&flush, fb, st));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    spmv_status_t s = cuda_status(cudaEventCreate(&e0));
+    if (s == SPMV_OK) s = cuda_status(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_form = SPMV_SPMM_WIDE;
+    for (int form = SPMV_SPMM_WIDE; form <= SPMV_SPMM_WIDE_GS6 && s == SPMV_OK; ++form) {
+        slot = form;
+        s = launch_spmm<T>(A, k, val, X, Y, st);
+        float t[3];
+        for (int i = 0; i < 3 && s == SPMV_OK; ++i) {
+            s = cuda_status(cudaMemsetAsync(flush, i + 1, fb, st));
+            if (s == SPMV_OK) s = cuda_status(cudaEventRecord(e0, st));
+            if (s == SPMV_OK) s = launch_spmm<T>(A, k, val, X, Y, st);
+            if (s == SPMV_OK) s = cuda_status(cudaEventRecord(e1, st));
+            if (s == SPMV_OK) s = cuda_status(cudaEventSynchronize(e1));
+            if (s == SPMV_OK) s = cuda_status(cudaEventElapsedTime(&t[i], e0, e1));
+        }
+        if (s != SPMV_OK) break;
+        const float med = std::max(std::min(t[0], t[1]), std::min(std::max(t[0], t[1]), t[2]));
+        if (med < best) {
+            best = med;
+            best_form = form;
+        }
+    }
+    slot = s == SPMV_OK ? best_form : SPMV_SPMM_AUTO;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFreeAsync(flush, st);
+    return s;
+}
+
 }  // namespace
+
+spmv_status_t tune_spmm64(spmv_matrix_t A, int k, const double *X, double *Y, cudaStream_t st) {
+    return tune_spmm<double>(A, k, A->sell_val.p, X, Y, st);
+}
+
+spmv_status_t tune_spmm32(spmv_matrix_t A, int k, const float *X, float *Y, cudaStream_t st) {
+    return tune_spmm<float>(A, k, A->sell_val32.p, X, Y, st);
+}
 
 spmv_status_t launch_spmm64(spmv_matrix_t A, int k, const double *X, double *Y, cudaStream_t st) {
     return launch_spmm<double>(A, k, A->sell_val.p, X, Y, st);

@@ -201,13 +201,20 @@ int kuhnbox_assemble(int64_t nx, int64_t ny, int64_t nz, const double *jit, cons
         }
     }
     /* rows in the permuted numbering, columns ascending; diagonal = minus the off-diagonals
-     * summed left to right in column order (+ the boundary sum for the Dirichlet variant) */
+     * summed left to right in column order (+ the boundary sum for the Dirichlet variant).
+     * Rows are written in the old cells' order (neighbours' new numbers are then read from
+     * nearby entries of inv), each at its place in the new order. */
     for (int64_t r = 0; r < n; ++r) inv[perm ? perm[r] : r] = (int32_t)r;
-    const double sign = dirichlet ? -1.0 : 1.0;
-    int64_t at = 0;
     row_ptr[0] = 0;
     for (int64_t r = 0; r < n; ++r) {
         const int64_t old = perm ? perm[r] : r;
+        int32_t len = 1;
+        for (int f = 0; f < 4; ++f) len += nb[4 * old + f] >= 0;
+        row_ptr[r + 1] = row_ptr[r] + len;
+    }
+    const double sign = dirichlet ? -1.0 : 1.0;
+    for (int64_t old = 0; old < n; ++old) {
+        const int64_t r = inv[old];
         int32_t cc[4];
         double vv[4];
         int m = 0;
@@ -228,6 +235,7 @@ int kuhnbox_assemble(int64_t nx, int64_t ny, int64_t nz, const double *jit, cons
         double diag = 0.0;
         for (int q = 0; q < m; ++q) diag = diag - vv[q];
         if (dirichlet) diag = diag + bdiag[old];
+        int64_t at = row_ptr[r];
         int placed = 0;
         for (int q = 0; q < m; ++q) {
             if (!placed && cc[q] > r) {
@@ -242,8 +250,8 @@ int kuhnbox_assemble(int64_t nx, int64_t ny, int64_t nz, const double *jit, cons
             col[at] = (int32_t)r;
             val[at++] = diag;
         }
-        row_ptr[r + 1] = (int32_t)at;
     }
+    const int64_t at = row_ptr[n];
     *nnz_out = at;
     free(cent); free(nb); free(nw); free(bdiag); free(inv);
     return 0;
