@@ -281,6 +281,17 @@ def run_profile_kernel(args):
         Yd = torch.empty_like(Xd)
         for _ in range(args.steps):
             A.apply_multi(Xd, Yd)
+    elif what == "mcg":
+        # multi-RHS CG on the 87^3 mixed mesh, k = 8 and 32, FP64 and mixed, 32 iterations each
+        for k in (8, 32):
+            m, Bv = workloads.mixed(87, seed=1, k=k)
+            A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values, reorder=capi.SPMV_REORDER_RCM,
+                            precision=capi.SPMV_PREC_DUAL, sigma=1024)
+            Bd = torch.from_numpy(np.ascontiguousarray(Bv.reshape(m.n, k)[A.permutation()])).to(dev)
+            Xd = torch.zeros_like(Bd)
+            for mixed in (0, 1):
+                A.solve_multi(Bd, Xd, rtol=1e-10, max_iter=32, mixed=mixed, max_outer=1)
+            A.close()
     elif what == "chain":
         M, G, L, rng = meshgen.kuhn_tet_operators(80, seed=0, permute=False)
         Gh = capi.Matrix(G.n, G.row_ptr, G.col_idx, G.values, n_cols=G.n_cols)
@@ -524,8 +535,10 @@ def summary_of(line):
             "mixed_vs_separate": r3(g("cg_multi_rhs", k, "speedup_mixed_vs_separate"))}
     out["spmm_frac"] = {k: r3(g("spmm_mixed_mesh", k, "roofline", "frac"))
                         for k in ("k8_f64", "k8_f32", "k32_f64", "k32_f32")}
-    out["chain_speedup"] = {"fp64": r3(g("operator_chain", "speedup")),
-                            "fp32": r3(g("operator_chain", "fp32", "speedup"))}
+    out["chain_speedup_tuned"] = {"fp64": r3(g("operator_chain", "speedup")),
+                                  "fp32": r3(g("operator_chain", "fp32", "speedup"))}
+    out["chain_speedup_fused_kernel"] = {"fp64": r3(g("operator_chain", "fused_speedup")),
+                                         "fp32": r3(g("operator_chain", "fp32", "fused_speedup"))}
     sv = g("serving")
     if sv:
         out["serving"] = {"requests": sv["requests"],
@@ -857,48 +870,54 @@ def mcg_results(args, torch, capi, workloads, dev):
 def chain_results(args, torch, capi, flush, stream, dev):
     """Operator chain of the operator-based formulation: y = M (G x) with the gradient G
     (faces x cells) and the divergence M (cells x faces) of the 80^3 Kuhn-tet mesh (3.07M
-    cells, 6.1M faces): two separate products against the fused chain."""
+    cells, 6.1M faces): two separate products called by the user against spmv_apply_chain in
+    each of its forms (the fused kernel, the two products through M's temporary) and with
+    the form its tuner picks on the first call."""
     from paper_2107_12371_gb300 import meshgen
     M, G, L, rng = meshgen.kuhn_tet_operators(80, seed=0, permute=False)
     x = meshgen.uniform_vectors(rng, L.n)
     Gh = capi.Matrix(G.n, G.row_ptr, G.col_idx, G.values, stream=stream, n_cols=G.n_cols,
                      precision=capi.SPMV_PREC_DUAL)
-    Mh = capi.Matrix(M.n, M.row_ptr, M.col_idx, M.values, stream=stream, n_cols=M.n_cols,
-                     precision=capi.SPMV_PREC_DUAL)
+    forms = {"fused": capi.SPMV_CHAIN_FUSED, "two_products": capi.SPMV_CHAIN_TWO,
+             "tuned": capi.SPMV_CHAIN_AUTO}
+    Mh = {name: capi.Matrix(M.n, M.row_ptr, M.col_idx, M.values, stream=stream,
+                            n_cols=M.n_cols, precision=capi.SPMV_PREC_DUAL, chain_form=f,
+                            autotune=int(f == capi.SPMV_CHAIN_AUTO))
+          for name, f in forms.items()}
     xd = torch.from_numpy(x).to(dev)
     t = torch.empty(G.n, dtype=torch.float64, device=dev)
     y = torch.empty(M.n, dtype=torch.float64, device=dev)
+    x32, t32, y32 = xd.float(), t.float(), y.float()
     K = max(10, min(args.steps, 50))
+    ms = lambda fn: (lambda ts: sum(ts) / len(ts))(time_kernel(torch, fn, K, flush, stream))  # noqa
 
     def sep():
         Gh.apply(xd, t, stream)
-        Mh.apply(t, y, stream)
-    ts = time_kernel(torch, sep, K, flush, stream)
-    tf = time_kernel(torch, lambda: capi.spmv_apply_chain(Mh.handle, Gh.handle, xd, y, stream),
-                     K, flush, stream)
-    ms_sep, ms_fused = sum(ts) / len(ts), sum(tf) / len(tf)
-    # FP32: the face values the fusion evaluates twice cost FP32 FMAs, which GB300 has plenty of
-    x32, t32 = xd.float(), t.float()
-    y32 = y.float()
+        Mh["fused"].apply(t, y, stream)
 
     def sep32():
         Gh.apply_f32(x32, t32, stream)
-        Mh.apply_f32(t32, y32, stream)
-    ts32 = time_kernel(torch, sep32, K, flush, stream)
-    tf32 = time_kernel(torch, lambda: capi.spmv_apply_chain_f32(Mh.handle, Gh.handle, x32, y32,
-                                                                 stream), K, flush, stream)
-    ms_sep32, ms_fused32 = sum(ts32) / len(ts32), sum(tf32) / len(tf32)
+        Mh["fused"].apply_f32(t32, y32, stream)
+    out = {"mesh": "kuhn-tet 80^3, %d cells, %d faces" % (L.n, G.n),
+           "separate_ms": ms(sep), "fp32": {"separate_ms": ms(sep32)}}
+    for name, h in Mh.items():
+        out[name + "_ms"] = ms(lambda: capi.spmv_apply_chain(h.handle, Gh.handle, xd, y, stream))
+        out["fp32"][name + "_ms"] = ms(lambda: capi.spmv_apply_chain_f32(h.handle, Gh.handle,
+                                                                          x32, y32, stream))
+    out["tuned_pick"] = {"fp64": Mh["tuned"].info()["chain_form"][0],
+                         "fp32": Mh["tuned"].info()["chain_form"][1],
+                         "codes": "1 fused kernel, 2 two products"}
+    out["speedup"] = out["separate_ms"] / out["tuned_ms"]
+    out["fp32"]["speedup"] = out["fp32"]["separate_ms"] / out["fp32"]["tuned_ms"]
+    out["fused_speedup"] = out["separate_ms"] / out["fused_ms"]
+    out["fp32"]["fused_speedup"] = out["fp32"]["separate_ms"] / out["fp32"]["fused_ms"]
     nbytes = 12 * (M.nnz + G.nnz) + 8 * (L.n + 2 * G.n + L.n)
+    out["algorithmic_bytes_two_products"] = nbytes
+    out["separate_GBs"] = nbytes / (out["separate_ms"] / 1e3) / 1e9
     Gh.close()
-    Mh.close()
-    return {"operator_chain": {
-        "mesh": "kuhn-tet 80^3, %d cells, %d faces" % (L.n, G.n),
-        "separate_ms": ms_sep, "fused_ms": ms_fused, "speedup": ms_sep / ms_fused,
-        "algorithmic_bytes_two_products": nbytes,
-        "separate_GBs": nbytes / (ms_sep / 1e3) / 1e9,
-        "fused_GBs_same_bytes": nbytes / (ms_fused / 1e3) / 1e9,
-        "fp32": {"separate_ms": ms_sep32, "fused_ms": ms_fused32,
-                 "speedup": ms_sep32 / ms_fused32}}}
+    for h in Mh.values():
+        h.close()
+    return {"operator_chain": out}
 
 
 def _gen_request(index, cells):

@@ -99,7 +99,16 @@ typedef struct {
     int pq_unroll;       /* CG product entries in flight per lane: 0 = tuned / automatic, 2, 5 */
     int gather_bytes;    /* cg_solve_multi: bytes of a row of P each product lane gathers
                           * (0 = tuned when autotune is on, else 32; 16 or 32) */
+    int chain_form;      /* spmv_apply_chain with this handle as B (SPMV_CHAIN_*): AUTO =
+                          * tuned on the first call when autotune is on, else TWO */
 } spmv_options_t;
+
+/* forms of the operator chain y = B (C x) (spmv_options_t.chain_form of B); both give the
+ * same y bit for bit */
+#define SPMV_CHAIN_AUTO 0
+#define SPMV_CHAIN_FUSED 1 /* one kernel: each entry b_if evaluates row f of C on the spot */
+#define SPMV_CHAIN_TWO 2   /* two sliced products through a temporary t = C x (C->n_rows
+                            * entries) that B's handle allocates on first use and keeps */
 
 /* forms of the 256-bit multi-vector product (spmv_options_t.spmm_form) */
 #define SPMV_SPMM_AUTO 0
@@ -172,6 +181,7 @@ typedef struct {
     int32_t pq_ctas;         /* CG product grid: CTAs per SM                        */
     int32_t pq_unroll;       /* CG product entries in flight per lane (FP64 handle)  */
     int32_t gather_bytes;    /* cg_solve_multi product: bytes gathered per lane      */
+    int32_t chain_form[2];   /* SPMV_CHAIN_* of spmv_apply_chain(_f32) with this B      */
 } spmv_info_t;
 spmv_status_t spmv_get_info(spmv_matrix_t A, spmv_info_t *info);
 
@@ -254,18 +264,23 @@ spmv_status_t spmv_apply_multi_f32(spmv_matrix_t A, int k, const float *X_dev, f
 
 /*
  * spmv_apply_chain -- async.  y = B (C x) for an operator chain (the operator-based formulation
- * evaluates a time step as chains of sparse products, Sec. 2), without writing C x to memory:
- * each entry b_if of B evaluates t_f = sum_j c_fj x_j over row f of C in column order with
- * fused multiply-add from +0.0, and y_i = sum_f b_if t_f in B's column order, so y equals
- * spmv_apply(B, spmv_apply(C, x)) bit for bit.  Requires B's columns = C's rows
+ * evaluates a time step as chains of sparse products, Sec. 2): each entry b_if of B meets
+ * t_f = sum_j c_fj x_j over row f of C in column order with fused multiply-add from +0.0, and
+ * y_i = sum_f b_if t_f in B's column order, so y equals spmv_apply(B, spmv_apply(C, x)) bit for
+ * bit.  Two forms compute it (B's chain_form option): one fused kernel that never writes C x
+ * (it evaluates each row of C once per entry of B naming it), or the two sliced products
+ * through a temporary t = C x kept by B's handle (allocated on the first call of that form,
+ * counted in device_bytes).  Unset (AUTO), the two products run -- measured faster on GB300,
+ * where t stays in L2 between them -- or, with autotune on, the first call times both forms
+ * (synchronizing the stream) and keeps the faster for B.  Requires B's columns = C's rows
  * (B->n_cols == C->n_rows) and neither handle renumbered (no reorder, no sigma); FP64 values.
  * x: device double[C n_cols]; y: device double[B n_rows], 16-byte aligned, not overlapping x.
  */
 spmv_status_t spmv_apply_chain(spmv_matrix_t B, spmv_matrix_t C, const double *x_dev,
                                double *y_dev, void *stream);
 
-/* async.  FP32 version of spmv_apply_chain (FP32 / DUAL handles): y equals
- * spmv_apply_f32(B, spmv_apply_f32(C, x)) bit for bit. */
+/* async.  FP32 version of spmv_apply_chain (FP32 / DUAL handles), with its own form choice:
+ * y equals spmv_apply_f32(B, spmv_apply_f32(C, x)) bit for bit. */
 spmv_status_t spmv_apply_chain_f32(spmv_matrix_t B, spmv_matrix_t C, const float *x_dev,
                                    float *y_dev, void *stream);
 

@@ -34,6 +34,7 @@ SPMV_VARIANT_AUTO, SPMV_VARIANT_CSR, SPMV_VARIANT_SELL, SPMV_VARIANT_SELL_WINDOW
 SPMV_VARIANT_SELL_BULK = 4
 SPMV_SPMM_AUTO, SPMV_SPMM_WIDE, SPMV_SPMM_WIDE_PIPE, SPMV_SPMM_WIDE_GS4, SPMV_SPMM_WIDE_GS6 = \
     0, 1, 2, 3, 4
+SPMV_CHAIN_AUTO, SPMV_CHAIN_FUSED, SPMV_CHAIN_TWO = 0, 1, 2
 
 
 class spmv_options_t(ctypes.Structure):
@@ -44,7 +45,7 @@ class spmv_options_t(ctypes.Structure):
                 ("index_bits", ctypes.c_int), ("sigma", ctypes.c_int),
                 ("checks", ctypes.c_int), ("spmm_form", ctypes.c_int),
                 ("pq_ctas", ctypes.c_int), ("pq_unroll", ctypes.c_int),
-                ("gather_bytes", ctypes.c_int)]
+                ("gather_bytes", ctypes.c_int), ("chain_form", ctypes.c_int)]
 
 
 class spmv_info_t(ctypes.Structure):
@@ -57,7 +58,7 @@ class spmv_info_t(ctypes.Structure):
                 ("device_bytes", ctypes.c_size_t), ("index_bits", ctypes.c_int32),
                 ("n_cols", ctypes.c_int32), ("spmm_form", (ctypes.c_int32 * 4) * 2),
                 ("pq_ctas", ctypes.c_int32), ("pq_unroll", ctypes.c_int32),
-                ("gather_bytes", ctypes.c_int32)]
+                ("gather_bytes", ctypes.c_int32), ("chain_form", ctypes.c_int32 * 2)]
 
 
 class cg_options_t(ctypes.Structure):
@@ -242,7 +243,8 @@ def spmv_get_info(h):
     out = {}
     for f, _ in spmv_info_t._fields_:
         v = getattr(info, f)
-        out[f] = [list(r) for r in v] if f == "spmm_form" else v
+        out[f] = ([list(r) for r in v] if f == "spmm_form" else
+                  list(v) if f == "chain_form" else v)
     return out
 
 

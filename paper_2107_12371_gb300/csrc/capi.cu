@@ -65,6 +65,8 @@ static spmv_status_t normalize_options(const spmv_options_t *in, spmv_options_t 
     if (o->pq_unroll != 0 && o->pq_unroll != 2 && o->pq_unroll != 5) return SPMV_ERR_INVALID_ARG;
     if (o->gather_bytes != 0 && o->gather_bytes != 16 && o->gather_bytes != 32)
         return SPMV_ERR_INVALID_ARG;
+    if (o->chain_form < SPMV_CHAIN_AUTO || o->chain_form > SPMV_CHAIN_TWO)
+        return SPMV_ERR_INVALID_ARG;
     return SPMV_OK;
 }
 
@@ -264,6 +266,8 @@ spmv_status_t spmv_get_info(spmv_matrix_t A, spmv_info_t *info) {
     info->pq_ctas = A->pq_ctas;
     info->pq_unroll = A->pq_unroll;
     info->gather_bytes = A->mcg_bytes;
+    info->chain_form[0] = chain_form_of(A, false);
+    info->chain_form[1] = chain_form_of(A, true);
     return SPMV_OK;
 }
 
@@ -433,6 +437,8 @@ void release_matrix(spmv_matrix_t A) {
     A->col_end.release(t);
     A->bulk_part.release(t);
     A->dev_status.release(t);
+    A->chain_t.release(t);
+    A->chain_t32.release(t);
     delete A;
 }
 

@@ -9,6 +9,10 @@
 // the intermediate vector C x is never written to or read back from HBM.  Each row of C is
 // evaluated once per entry of B that names it (twice for the face operators of a mesh); the
 // second evaluation finds C's row in L2 when B's rows follow C's numbering closely.
+// spmv_apply_chain runs either this kernel or the two sliced products through a temporary
+// t = C x kept by B's handle (chosen by option or by timing both; see run_chain).
+#include <algorithm>
+
 #include "common.cuh"
 #include "ptx.cuh"
 
@@ -69,6 +73,17 @@ spmv_status_t go_chain(spmv_matrix_t B, spmv_matrix_t C, const T *bval, const T 
     return SPMV_OK;
 }
 
+template <typename T>
+DevBuf<T> &chain_tmp(spmv_matrix_t B);
+template <>
+DevBuf<double> &chain_tmp<double>(spmv_matrix_t B) {
+    return B->chain_t;
+}
+template <>
+DevBuf<float> &chain_tmp<float>(spmv_matrix_t B) {
+    return B->chain_t32;
+}
+
 spmv_status_t check_chain(spmv_matrix_t B, spmv_matrix_t C, const void *x, const void *y) {
     if (!B || !C || B->n_cols != C->n) return SPMV_ERR_INVALID_ARG;
     if (B->perm.p || C->perm.p) return SPMV_ERR_INVALID_ARG;  // numberings must compose as given
@@ -78,7 +93,106 @@ spmv_status_t check_chain(spmv_matrix_t B, spmv_matrix_t C, const void *x, const
     return SPMV_OK;
 }
 
+// Kernel launches of one form of the chain (fused kernel, or the two sliced products through
+// the temporary t = C x that B's handle keeps).
+template <typename T>
+spmv_status_t chain_form_launch(spmv_matrix_t B, spmv_matrix_t C, int form, const T *x, T *y,
+                                cudaStream_t st) {
+    if (form == SPMV_CHAIN_TWO) {
+        DevBuf<T> &t = chain_tmp<T>(B);
+        if (t.n < (size_t)(C->n > 0 ? C->n : 1)) {
+            AllocStream scope(st);
+            GB_TRY(t.alloc((size_t)(C->n > 0 ? C->n : 1), &B->bytes));
+        }
+        if constexpr (sizeof(T) == 8) {
+            GB_TRY(launch_spmv64(C, x, t.p, st));
+            return launch_spmv64(B, t.p, y, st);
+        } else {
+            GB_TRY(launch_spmv32(C, x, t.p, st));
+            return launch_spmv32(B, t.p, y, st);
+        }
+    }
+    const T *bv, *cv;
+    if constexpr (sizeof(T) == 8) {
+        bv = B->sell_val.p;
+        cv = C->val.p;
+        switch (B->S) {
+            case 32: return go_chain<T, 1, 32>(B, C, bv, cv, x, y, st);
+            case 64: return go_chain<T, 2, 32>(B, C, bv, cv, x, y, st);
+            case 128: return go_chain<T, 4, 32>(B, C, bv, cv, x, y, st);
+            case 256: return go_chain<T, 8, 32>(B, C, bv, cv, x, y, st);
+        }
+    } else {
+        bv = B->sell_val32.p;
+        cv = C->val32.p;
+        switch (B->S) {  // (R, L) of the FP32 sliced kernels
+            case 32: return go_chain<T, 4, 8>(B, C, bv, cv, x, y, st);
+            case 64: return go_chain<T, 4, 16>(B, C, bv, cv, x, y, st);
+            case 128: return go_chain<T, 4, 32>(B, C, bv, cv, x, y, st);
+            case 256: return go_chain<T, 8, 32>(B, C, bv, cv, x, y, st);
+        }
+    }
+    return SPMV_ERR_INVALID_ARG;
+}
+
+// Form for this call: B's option, else B's tuned pick for the precision, else (untuned) the
+// two products, measured faster on GB300 in both precisions (t = C x stays in L2 between them,
+// while the fused kernel evaluates each row of C once per entry of B that names it).  With
+// autotune on, the first call times both forms (the median of three launches each after
+// overwriting L2) and keeps the faster; either form leaves the same y.
+template <typename T>
+spmv_status_t run_chain(spmv_matrix_t B, spmv_matrix_t C, const T *x, T *y, cudaStream_t st) {
+    if (B->opt.chain_form != SPMV_CHAIN_AUTO)
+        return chain_form_launch<T>(B, C, B->opt.chain_form, x, y, st);
+    int &pick = B->chain_pick[sizeof(T) == 4 ? 1 : 0];
+    if (pick == SPMV_CHAIN_AUTO && B->opt.autotune) {
+        const size_t fb = 2 * (size_t)(device_facts().l2_bytes > 0 ? device_facts().l2_bytes
+                                                                   : (128 << 20));
+        void *flush = nullptr;
+        {
+            AllocStream scope(st);
+            GB_CUDA(gb_malloc_async(&flush, fb, st));
+        }
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        spmv_status_t s = cuda_status(cudaEventCreate(&e0));
+        if (s == SPMV_OK) s = cuda_status(cudaEventCreate(&e1));
+        float best = 1e30f;
+        int best_form = SPMV_CHAIN_TWO;
+        for (int form : {SPMV_CHAIN_FUSED, SPMV_CHAIN_TWO}) {
+            float t[3] = {0.f, 0.f, 0.f};
+            for (int i = -1; i < 3 && s == SPMV_OK; ++i) {  // i = -1: warm-up
+                s = cuda_status(cudaMemsetAsync(flush, i + 2, fb, st));
+                if (s == SPMV_OK) s = cuda_status(cudaEventRecord(e0, st));
+                if (s == SPMV_OK) s = chain_form_launch<T>(B, C, form, x, y, st);
+                if (s == SPMV_OK) s = cuda_status(cudaEventRecord(e1, st));
+                if (s == SPMV_OK) s = cuda_status(cudaEventSynchronize(e1));
+                if (s == SPMV_OK && i >= 0) s = cuda_status(cudaEventElapsedTime(&t[i], e0, e1));
+            }
+            if (s != SPMV_OK) break;
+            const float med =
+                std::max(std::min(t[0], t[1]), std::min(std::max(t[0], t[1]), t[2]));
+            if (med < best) {
+                best = med;
+                best_form = form;
+            }
+        }
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        cudaFreeAsync(flush, st);
+        GB_TRY(s);
+        pick = best_form;
+    }
+    return chain_form_launch<T>(B, C, pick == SPMV_CHAIN_AUTO ? SPMV_CHAIN_TWO : pick, x, y, st);
+}
+
 }  // namespace
+
+int chain_form_of(const spmv_matrix_t B, bool f32) {
+    if (B->opt.chain_form != SPMV_CHAIN_AUTO) return B->opt.chain_form;
+    const int p = B->chain_pick[f32 ? 1 : 0];
+    return p == SPMV_CHAIN_AUTO ? SPMV_CHAIN_TWO : p;
+}
+
 }  // namespace gb
 
 using namespace gb;
@@ -88,15 +202,7 @@ extern "C" spmv_status_t spmv_apply_chain(spmv_matrix_t B, spmv_matrix_t C, cons
     GB_TRY(check_chain(B, C, x, y));
     if (!B->has64() || !C->has64()) return SPMV_ERR_UNSUPPORTED;
     if (B->n == 0) return SPMV_OK;
-    cudaStream_t st = (cudaStream_t)stream;
-    const double *bv = B->sell_val.p, *cv = C->val.p;
-    switch (B->S) {
-        case 32: return go_chain<double, 1, 32>(B, C, bv, cv, x, y, st);
-        case 64: return go_chain<double, 2, 32>(B, C, bv, cv, x, y, st);
-        case 128: return go_chain<double, 4, 32>(B, C, bv, cv, x, y, st);
-        case 256: return go_chain<double, 8, 32>(B, C, bv, cv, x, y, st);
-    }
-    return SPMV_ERR_INVALID_ARG;
+    return run_chain<double>(B, C, x, y, (cudaStream_t)stream);
 }
 
 extern "C" spmv_status_t spmv_apply_chain_f32(spmv_matrix_t B, spmv_matrix_t C, const float *x,
@@ -104,13 +210,5 @@ extern "C" spmv_status_t spmv_apply_chain_f32(spmv_matrix_t B, spmv_matrix_t C, 
     GB_TRY(check_chain(B, C, x, y));
     if (!B->has32() || !C->has32()) return SPMV_ERR_UNSUPPORTED;
     if (B->n == 0) return SPMV_OK;
-    cudaStream_t st = (cudaStream_t)stream;
-    const float *bv = B->sell_val32.p, *cv = C->val32.p;
-    switch (B->S) {  // (R, L) of the FP32 sliced kernels
-        case 32: return go_chain<float, 4, 8>(B, C, bv, cv, x, y, st);
-        case 64: return go_chain<float, 4, 16>(B, C, bv, cv, x, y, st);
-        case 128: return go_chain<float, 4, 32>(B, C, bv, cv, x, y, st);
-        case 256: return go_chain<float, 8, 32>(B, C, bv, cv, x, y, st);
-    }
-    return SPMV_ERR_INVALID_ARG;
+    return run_chain<float>(B, C, x, y, (cudaStream_t)stream);
 }

@@ -183,6 +183,11 @@ struct spmv_matrix_s {
     // SpMM form per precision (0 FP64, 1 FP32) and lanes per row (1, 2, 4, 8) chosen by the
     // tuner on the first multi-vector product of that shape (SPMV_SPMM_AUTO: not tuned)
     int spmm_tuned[2][4] = {};
+    // spmv_apply_chain with this handle as B: form picked per precision (SPMV_CHAIN_AUTO: not
+    // tuned) and the temporaries t = C x of the two-product form
+    int chain_pick[2] = {};
+    gb::DevBuf<double> chain_t;
+    gb::DevBuf<float> chain_t32;
 
     // spmv_apply_host(_async): two staging sets used in turn, each with device copies of x and
     // y, two streams of its own (product, device-to-host) and events; created on first use
@@ -222,6 +227,7 @@ spmv_status_t launch_spmm32(spmv_matrix_t A, int k, const float *X, float *Y, cu
 spmv_status_t tune_spmm64(spmv_matrix_t A, int k, const double *X, double *Y, cudaStream_t st);
 spmv_status_t tune_spmm32(spmv_matrix_t A, int k, const float *X, float *Y, cudaStream_t st);
 int spmm_form_of(const spmv_matrix_t A, bool f32, int gi);
+int chain_form_of(const spmv_matrix_t B, bool f32);
 spmv_status_t launch_permute(spmv_matrix_t A, int direction, int elem_bytes, const void *in,
                              void *out, cudaStream_t st);
 int window_capacity_words(int elem_bytes);

@@ -271,13 +271,22 @@ def test_rectangular_operators_parity(oracle):
     lx = oracle.spmv(L.row_ptr, L.col_idx, L.values, x)
     scale = np.add.reduceat(np.abs(L.values), L.row_ptr[:-1]) * np.abs(x).max()
     assert np.all(np.abs(y.cpu().numpy() - lx) <= 1e-13 * scale)
-    # the fused chain: y = M (G x) without writing G x, bit-identical to the two products
+    # the chain y = M (G x), every form (the fused kernel that never writes G x, the two
+    # products through the handle's temporary, the untuned default, the tuned pick),
+    # bit-identical to the two oracle products
     for S in (32, 64, 128, 256):
-        Ms = capi.Matrix(M.n, M.row_ptr, M.col_idx, M.values, n_cols=M.n_cols, slice_height=S)
-        yc = torch.empty_like(y)
-        capi.spmv_apply_chain(Ms.handle, Gh.handle, xd, yc)
-        torch.cuda.synchronize()
-        assert np.array_equal(yc.cpu().numpy(), ref_y), S
+        for form, tune in ((capi.SPMV_CHAIN_FUSED, 0), (capi.SPMV_CHAIN_TWO, 0),
+                           (capi.SPMV_CHAIN_AUTO, 0), (capi.SPMV_CHAIN_AUTO, 1)):
+            Ms = capi.Matrix(M.n, M.row_ptr, M.col_idx, M.values, n_cols=M.n_cols,
+                             slice_height=S, chain_form=form, autotune=tune)
+            for _ in range(2):  # the first call of a tuned handle times both forms
+                yc = torch.full_like(y, float("nan"))
+                capi.spmv_apply_chain(Ms.handle, Gh.handle, xd, yc)
+                torch.cuda.synchronize()
+                assert np.array_equal(yc.cpu().numpy(), ref_y), (S, form, tune)
+            picked = Ms.info()["chain_form"][0]
+            assert picked == (form if form else (picked if tune else capi.SPMV_CHAIN_TWO))
+            assert picked in (capi.SPMV_CHAIN_FUSED, capi.SPMV_CHAIN_TWO)
     # the FP32 chain equals the two FP32 products and the FP32 oracle, bit for bit
     G32 = capi.Matrix(G.n, G.row_ptr, G.col_idx, G.values, n_cols=G.n_cols,
                       precision=capi.SPMV_PREC_FP32)
@@ -285,12 +294,14 @@ def test_rectangular_operators_parity(oracle):
     ref_g32 = oracle.spmv_f32(G.row_ptr, G.col_idx, G.values.astype(np.float32), x32)
     ref_y32 = oracle.spmv_f32(M.row_ptr, M.col_idx, M.values.astype(np.float32), ref_g32)
     for S in (32, 64, 128, 256):
-        M32 = capi.Matrix(M.n, M.row_ptr, M.col_idx, M.values, n_cols=M.n_cols, slice_height=S,
-                          precision=capi.SPMV_PREC_DUAL)
-        y32 = torch.empty(M.n, dtype=torch.float32, device="cuda")
-        capi.spmv_apply_chain_f32(M32.handle, G32.handle, dev(x32), y32)
-        torch.cuda.synchronize()
-        assert np.array_equal(y32.cpu().numpy(), ref_y32), S
+        for form in (capi.SPMV_CHAIN_FUSED, capi.SPMV_CHAIN_TWO, capi.SPMV_CHAIN_AUTO):
+            M32 = capi.Matrix(M.n, M.row_ptr, M.col_idx, M.values, n_cols=M.n_cols,
+                              slice_height=S, precision=capi.SPMV_PREC_DUAL, chain_form=form,
+                              autotune=int(form == capi.SPMV_CHAIN_AUTO))
+            y32 = torch.empty(M.n, dtype=torch.float32, device="cuda")
+            capi.spmv_apply_chain_f32(M32.handle, G32.handle, dev(x32), y32)
+            torch.cuda.synchronize()
+            assert np.array_equal(y32.cpu().numpy(), ref_y32), (S, form)
     with pytest.raises(capi.SpmvError) as e:  # an FP64-only handle has no FP32 values
         capi.spmv_apply_chain_f32(Mh.handle, G32.handle, dev(x32),
                                   torch.empty(M.n, dtype=torch.float32, device="cuda"))
