@@ -438,6 +438,99 @@ spmv_status_t cg_solve_csr_noalloc(int32_t n, int64_t nnz, const int32_t *row_pt
                                    const double *b_dev, double *x_dev, const cg_options_t *opt,
                                    cg_result_t *result, void *stream);
 
+/* ------------------------------ row-block partition with halo exchange ------------------ */
+/*
+ * A square matrix split into n_parts contiguous row blocks, one per GPU (or per process), for
+ * matrices that do not fit one device or solves spread over several.  Not in the paper (its
+ * kernel runs on one FPGA); after an RCM order (Sec. 4.1) each block's rows read columns of
+ * their own block and of the neighbouring blocks only, so the exchange before each product is
+ * a small halo.  Part p owns rows [row_begin[p], row_begin[p + 1]).  Its extended vector
+ * x_ext = [halo below (n_halo_lo) | own entries (n_local) | halo above (n_halo_hi)] holds the
+ * halo entries in increasing global column order, and its matrix is stored with columns
+ * renumbered into x_ext monotonically, so each of its rows is the whole matrix's row in the
+ * same column order: the parts' products concatenated equal spmv_apply on the whole matrix
+ * bit for bit.  Exchange: part p sends to each part q (q ascending) the entries of its own x
+ * that q's halo reads (send lists: own rows in increasing order), and receives from each q one
+ * contiguous run of its halo (q ascending: the runs below its rows fill the low halo, those
+ * above the high halo).
+ */
+typedef struct spmv_part_s *spmv_part_t;
+
+typedef struct {
+    int32_t n_parts, part;
+    int32_t row_begin, row_end;  /* own rows (global numbering)                      */
+    int32_t n_local;             /* row_end - row_begin                              */
+    int32_t n_halo_lo;           /* halo entries with global column < row_begin      */
+    int32_t n_halo_hi;           /* halo entries with global column >= row_end       */
+    int32_t n_ext;               /* n_halo_lo + n_local + n_halo_hi                  */
+    int64_t nnz_local;
+    int32_t send_total;          /* entries this part sends per exchange             */
+    int32_t recv_total;          /* n_halo_lo + n_halo_hi                            */
+    size_t device_bytes;
+} spmv_part_info_t;
+
+/*
+ * spmv_partition_create -- sync.  Part `part` of the partition of the square CSR matrix
+ * (n rows, host arrays with the layout and checks of spmv_create, global numbering -- apply an
+ * RCM order before partitioning, e.g. with spmv_get_permutation / spmv_export_csr of a
+ * reordered handle).  row_begin: host int32[n_parts + 1], 0 = row_begin[0] <= ... <=
+ * row_begin[n_parts] = n.  1 <= n_parts <= 4096.  on_device = 0 builds only the host-side plan
+ * (halo, send lists, the part's CSR in the x_ext numbering: no CUDA call is made, for hosts
+ * without a GPU); on_device = 1 also builds the part's device handle (opt as for spmv_create;
+ * reorder and sigma must stay off so the global column order is kept).  Errors: INVALID_ARG,
+ * INVALID_CSR (checked on the host), OOM, CUDA.
+ */
+spmv_status_t spmv_partition_create(int32_t n, int64_t nnz, const int32_t *row_ptr,
+                                    const int32_t *col_idx, const double *values, int n_parts,
+                                    const int32_t *row_begin, int part, int on_device,
+                                    const spmv_options_t *opt, void *stream, spmv_part_t *out);
+spmv_status_t spmv_partition_destroy(spmv_part_t P);
+spmv_status_t spmv_partition_info(spmv_part_t P, spmv_part_info_t *info);
+
+/* Host copies of the exchange plan (any output may be NULL): send_counts[n_parts] and
+ * recv_counts[n_parts] (entries sent to / received from each part, 0 for itself),
+ * send_rows[send_total] (own rows to send, local numbering, grouped by destination part
+ * ascending), halo_cols[recv_total] (the halo's global columns, ascending). */
+spmv_status_t spmv_partition_lists(spmv_part_t P, int32_t *send_counts, int32_t *recv_counts,
+                                   int32_t *send_rows, int32_t *halo_cols);
+
+/* Host copy of the part's CSR: row_ptr[n_local + 1], col_idx[nnz_local] (x_ext numbering),
+ * values[nnz_local] (may be NULL). */
+spmv_status_t spmv_partition_local_csr(spmv_part_t P, int32_t *row_ptr, int32_t *col_idx,
+                                       double *values);
+
+/* async.  send_dev[i] = x_own_dev[send_rows[i]] for the whole send list (device double
+ * arrays: x_own of n_local entries -- the own part of an x_ext -- and send of send_total). */
+spmv_status_t spmv_partition_pack(spmv_part_t P, const double *x_own_dev, double *send_dev,
+                                  void *stream);
+
+/* async.  y = A_part x_ext: x_ext device double[n_ext] with its halo in place, y device
+ * double[n_local] (16-byte aligned, not overlapping). */
+spmv_status_t spmv_partition_apply(spmv_part_t P, const double *x_ext_dev, double *y_dev,
+                                   void *stream);
+
+/* Transport callbacks of cg_solve_partitioned, called on the calling host thread with the
+ * stream synchronised; each returns 0 on success.  exchange: send the part's send buffer
+ * (device double[send_total], grouped by destination ascending) and fill recv (device
+ * double[recv_total]) with the runs received from every other part, ascending.  allreduce:
+ * replace values_host[0..count) by their sum over all parts. */
+typedef int (*spmv_exchange_fn)(const double *send_dev, double *recv_dev, void *ctx);
+typedef int (*spmv_allreduce_fn)(double *values_host, int count, void *ctx);
+
+/*
+ * cg_solve_partitioned -- sync, called by every part at once.  FP64 Jacobi-PCG of the
+ * partitioned system: each part keeps its own rows of x, r, p, q; per iteration one halo
+ * exchange of p and two scalar all-reduces (p.q; then r.(D^-1 r) and r.r), the recurrence of
+ * cg_solve (its true-residual restarts excepted).  b_dev, x_dev: device double[n_local]; x
+ * holds x0 when opt->use_x0.  result->rel_residual is the true ||b - A x|| / ||b|| over all
+ * parts.  NOT_CONVERGED at the iteration cap; INVALID_CSR when any part has a row without a
+ * non-zero diagonal; opt->mixed / persistent: UNSUPPORTED; a failing callback: CUDA.
+ */
+spmv_status_t cg_solve_partitioned(spmv_part_t P, const double *b_dev, double *x_dev,
+                                   const cg_options_t *opt, cg_result_t *result,
+                                   spmv_exchange_fn exchange, spmv_allreduce_fn allreduce,
+                                   void *ctx, void *stream);
+
 /* ------------------------------ continuous-batching server ------------------------------ */
 typedef struct {
     uint64_t submitted, completed, rejected;

@@ -61,6 +61,15 @@ class spmv_info_t(ctypes.Structure):
                 ("gather_bytes", ctypes.c_int32), ("chain_form", ctypes.c_int32 * 2)]
 
 
+class spmv_part_info_t(ctypes.Structure):
+    _fields_ = [("n_parts", ctypes.c_int32), ("part", ctypes.c_int32),
+                ("row_begin", ctypes.c_int32), ("row_end", ctypes.c_int32),
+                ("n_local", ctypes.c_int32), ("n_halo_lo", ctypes.c_int32),
+                ("n_halo_hi", ctypes.c_int32), ("n_ext", ctypes.c_int32),
+                ("nnz_local", ctypes.c_int64), ("send_total", ctypes.c_int32),
+                ("recv_total", ctypes.c_int32), ("device_bytes", ctypes.c_size_t)]
+
+
 class cg_options_t(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("max_iter", ctypes.c_int), ("mixed", ctypes.c_int),
                 ("inner_rtol", ctypes.c_double), ("max_outer", ctypes.c_int),
@@ -136,7 +145,21 @@ _SIGS = {
     "spmv_device_status": [_P, _P],
     "spmv_diag_bulk_timeout": [_P, _P],
     "spmv_diag_checks": [_P, ctypes.POINTER(_int), ctypes.POINTER(_int), _P],
+    "spmv_partition_create": [_i32, _i64, _P, _P, _P, _int, _P, _int, _int,
+                              ctypes.POINTER(spmv_options_t), _P, ctypes.POINTER(_P)],
+    "spmv_partition_destroy": [_P],
+    "spmv_partition_info": [_P, ctypes.POINTER(spmv_part_info_t)],
+    "spmv_partition_lists": [_P, _P, _P, _P, _P],
+    "spmv_partition_local_csr": [_P, _P, _P, _P],
+    "spmv_partition_pack": [_P, _P, _P, _P],
+    "spmv_partition_apply": [_P, _P, _P, _P],
+    "cg_solve_partitioned": [_P, _P, _P, ctypes.POINTER(cg_options_t),
+                             ctypes.POINTER(cg_result_t), _P, _P, _P, _P],
 }
+
+# transport callbacks of cg_solve_partitioned
+EXCHANGE_FN = ctypes.CFUNCTYPE(_int, _P, _P, _P)
+ALLREDUCE_FN = ctypes.CFUNCTYPE(_int, ctypes.POINTER(ctypes.c_double), _int, _P)
 
 _lib = None
 
@@ -407,6 +430,94 @@ def cg_solve_multi(h, k, B, X, options=None, stream=None):
     cols = [dict(iterations=r.iterations, outer_iterations=r.outer_iterations,
                  rel_residual=r.rel_residual, status=r.status) for r in res]
     return st, cols
+
+
+class Partition:
+    """One part of a row-block partition (spmv_partition_*): the host plan (halo, send lists,
+    the part's CSR) and, with on_device, its device handle."""
+
+    def __init__(self, n, row_ptr, col_idx, values, row_begin, part, on_device=True,
+                 stream=None, **options):
+        row_ptr = np.ascontiguousarray(row_ptr, np.int32)
+        col_idx = np.ascontiguousarray(col_idx, np.int32)
+        values = np.ascontiguousarray(values, np.float64)
+        rb = np.ascontiguousarray(row_begin, np.int32)
+        h = _P()
+        opt = spmv_default_options(**options)
+        _check(load().spmv_partition_create(int(n), int(col_idx.size), row_ptr.ctypes.data,
+                                            col_idx.ctypes.data, values.ctypes.data,
+                                            int(rb.size - 1), rb.ctypes.data, int(part),
+                                            int(bool(on_device)), ctypes.byref(opt),
+                                            _stream(stream) if on_device else None,
+                                            ctypes.byref(h)), "spmv_partition_create")
+        self.handle = h.value
+        self.n_parts = int(rb.size - 1)
+        info = spmv_part_info_t()
+        _check(load().spmv_partition_info(self.handle, ctypes.byref(info)), "spmv_partition_info")
+        self.info = {f: getattr(info, f) for f, _ in spmv_part_info_t._fields_}
+        sc = np.zeros(self.n_parts, np.int32)
+        rc = np.zeros(self.n_parts, np.int32)
+        sr = np.zeros(max(1, self.info["send_total"]), np.int32)
+        hc = np.zeros(max(1, self.info["recv_total"]), np.int32)
+        _check(load().spmv_partition_lists(self.handle, sc.ctypes.data, rc.ctypes.data,
+                                           sr.ctypes.data, hc.ctypes.data),
+               "spmv_partition_lists")
+        self.send_counts, self.recv_counts = sc, rc
+        self.send_rows = sr[:self.info["send_total"]]
+        self.halo_cols = hc[:self.info["recv_total"]]
+
+    def local_csr(self):
+        nl, nz = self.info["n_local"], self.info["nnz_local"]
+        rp = np.zeros(nl + 1, np.int32)
+        ci = np.zeros(max(1, nz), np.int32)
+        v = np.zeros(max(1, nz), np.float64)
+        _check(load().spmv_partition_local_csr(self.handle, rp.ctypes.data, ci.ctypes.data,
+                                               v.ctypes.data), "spmv_partition_local_csr")
+        return rp, ci[:nz], v[:nz]
+
+    def pack(self, x_own, send, stream=None):
+        _check(load().spmv_partition_pack(self.handle, _ptr(x_own), _ptr(send), _stream(stream)),
+               "spmv_partition_pack")
+
+    def apply(self, x_ext, y, stream=None):
+        _check(load().spmv_partition_apply(self.handle, _ptr(x_ext), _ptr(y), _stream(stream)),
+               "spmv_partition_apply")
+
+    def solve(self, b, x, exchange, allreduce, stream=None, **cg_opts):
+        """cg_solve_partitioned with Python transport callbacks exchange(send_ptr, recv_ptr)
+        and allreduce(values: numpy view) (each returns nothing; an exception fails the
+        solve)."""
+        def ex(send_p, recv_p, _ctx):
+            try:
+                exchange(send_p, recv_p)
+                return 0
+            except Exception:  # reported to the C side as a failed transport
+                return 1
+
+        def ar(vals, count, _ctx):
+            try:
+                allreduce(np.ctypeslib.as_array(vals, shape=(count,)))
+                return 0
+            except Exception:
+                return 1
+        ex_c, ar_c = EXCHANGE_FN(ex), ALLREDUCE_FN(ar)
+        res = cg_result_t()
+        st = load().cg_solve_partitioned(self.handle, _ptr(b), _ptr(x),
+                                         ctypes.byref(cg_default_options(**cg_opts)),
+                                         ctypes.byref(res), ex_c, ar_c, None, _stream(stream))
+        return dict(iterations=res.iterations, outer_iterations=res.outer_iterations,
+                    rel_residual=res.rel_residual, status=st)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().spmv_partition_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 SPMV_NOALLOC_MAX_ROWS = 65536
