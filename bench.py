@@ -771,6 +771,13 @@ def cg_results(torch, capi, m, b, A, bi, dev):
     best64 = min(out["cg_fp64_graph"]["seconds"], out["cg_fp64_persistent"]["seconds"])
     best32 = min(out["cg_mixed_ir"]["seconds"], out["cg_mixed_ir_persistent"]["seconds"])
     out["mixed_speedup_vs_fp64"] = best64 / best32
+    # where an FP64 iteration's time goes (CUDA events; the solve above ran 16-iteration graph
+    # batches with a scalar read-back after each)
+    t = capi.spmv_diag_cg_timing(A.handle, 64)
+    t["kernel_sum"] = t["product"] + t["update_xr"] + t["update_p"]
+    t["solve_per_iter"] = out["cg_fp64_graph"]["ms_per_iteration"]
+    t["unit"] = "ms"
+    out["cg_iteration_breakdown"] = t
     return out
 
 

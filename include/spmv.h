@@ -393,6 +393,18 @@ spmv_status_t cg_solve_multi(spmv_matrix_t A, int k, const double *B_dev, double
                              const cg_options_t *opt, cg_result_t *results, void *stream);
 
 /*
+ * spmv_diag_cg_timing -- sync.  Diagnostic of where an FP64 CG iteration's time goes on this
+ * handle (not in the paper): the recurrence runs on b = 1 with no stopping test, and CUDA events
+ * on `stream` time ms_out[0] one CUDA-graph batch of `iters` iterations, per iteration;
+ * ms_out[1] the same kernels launched directly on the stream, per iteration; ms_out[2..4] the
+ * product, the x/r sweep and the p sweep each between events of their own, per launch;
+ * ms_out[5] a read-back of the scalar block to the host (the solve's convergence check), per
+ * read.  ms_out: host double[6].  1 <= iters <= 4096.  Overwrites the handle's solve state.
+ * INVALID_ARG for an empty or rectangular handle, UNSUPPORTED without FP64 values.
+ */
+spmv_status_t spmv_diag_cg_timing(spmv_matrix_t A, int iters, double *ms_out, void *stream);
+
+/*
  * spmv_diag_barrier_timeout -- sync.  Self-test of the failure path of the persistent CG
  * kernel's bounded waits (not in the paper): launches `ctas` co-resident CTAs (1 <= ctas <= SM
  * count) on the kernel's grid barrier configured to expect one CTA more than exist, so no
@@ -569,6 +581,14 @@ spmv_status_t spmv_server_poll(spmv_server_t s, uint64_t ticket, double *x_host,
                                cg_result_t *result);
 
 spmv_status_t spmv_server_get_stats(spmv_server_t s, spmv_server_stats_t *stats);
+
+/* Requests whose estimated device footprint (the admission estimate) is at least `bytes` run
+ * their kernels on a stream of the device's highest priority, so that when solves compete for
+ * the SMs the large ones -- the tail of the latency distribution -- are scheduled first; 0
+ * (the default) runs every request at the default priority.  Applies to requests admitted
+ * after the call.  Results are unchanged (each request's kernels and reductions are the same
+ * whatever stream runs them).  Server-side only: no counterpart in the paper. */
+spmv_status_t spmv_server_set_priority_bytes(spmv_server_t s, size_t bytes);
 
 /* Cancels a request.  A queued request never starts; a running solve stops at its next
  * convergence check (after each CUDA-graph batch of check_every iterations; a small system

@@ -129,6 +129,7 @@ _SIGS = {
     "cg_solve_multi": [_P, _int, _P, _P, ctypes.POINTER(cg_options_t),
                        ctypes.POINTER(cg_result_t), _P],
     "spmv_diag_barrier_timeout": [_int, ctypes.c_double, _P],
+    "spmv_diag_cg_timing": [_P, _int, _P, _P],
     "cg_solve_csr_noalloc": [_i32, _i64, _P, _P, _P, _P, _P, ctypes.POINTER(cg_options_t),
                              ctypes.POINTER(cg_result_t), _P],
     "spmv_server_create": [ctypes.c_size_t, _int, ctypes.POINTER(_P)],
@@ -136,6 +137,7 @@ _SIGS = {
                            ctypes.POINTER(ctypes.c_uint64)],
     "spmv_server_poll": [_P, ctypes.c_uint64, _P, ctypes.POINTER(cg_result_t)],
     "spmv_server_get_stats": [_P, ctypes.POINTER(spmv_server_stats_t)],
+    "spmv_server_set_priority_bytes": [_P, ctypes.c_size_t],
     "spmv_server_destroy": [_P],
     "spmv_server_cancel": [_P, ctypes.c_uint64],
     "spmv_apply_host": [_P, _P, _P, _P],
@@ -293,6 +295,16 @@ def spmv_diag_bulk_timeout(h, stream=None):
     """Self-test of the staged product's bounded wait; returns the status (SPMV_ERR_TIMEOUT is
     the expected outcome)."""
     return load().spmv_diag_bulk_timeout(h, _stream(stream))
+
+
+def spmv_diag_cg_timing(h, iters, stream=None):
+    """Per-iteration times (ms) of an FP64 CG iteration: graph batch, direct launches, the three
+    kernels each alone, and a scalar read-back (spmv_diag_cg_timing)."""
+    out = np.zeros(6)
+    _check(load().spmv_diag_cg_timing(h, int(iters), out.ctypes.data, _stream(stream)),
+           "spmv_diag_cg_timing")
+    return dict(zip(("graph_per_iter", "direct_per_iter", "product", "update_xr", "update_p",
+                     "scalar_readback"), out.tolist()))
 
 
 def spmv_diag_checks(h, stream=None):
@@ -569,6 +581,10 @@ def spmv_server_get_stats(s):
     stt = spmv_server_stats_t()
     _check(load().spmv_server_get_stats(s, ctypes.byref(stt)), "spmv_server_get_stats")
     return {f: getattr(stt, f) for f, _ in spmv_server_stats_t._fields_}
+
+
+def spmv_server_set_priority_bytes(s, nbytes):
+    _check(load().spmv_server_set_priority_bytes(s, int(nbytes)), "spmv_server_set_priority_bytes")
 
 
 def spmv_server_cancel(s, ticket):

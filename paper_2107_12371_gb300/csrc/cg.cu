@@ -759,11 +759,92 @@ void release_cg(spmv_matrix_t A) {
     w = CgWork{};
 }
 
+// Times (CUDA events on `st`) of the FP64 iteration of this handle, for the diagnostic entry
+// point below: out[0] a CUDA-graph batch of `iters` iterations, per iteration; out[1] the same
+// kernels launched directly on the stream, per iteration; out[2..4] each kernel of an
+// iteration between events of its own (product, x/r sweep, p sweep); out[5] a read-back of
+// the scalars to the host (copy + synchronisation).  The recurrence runs on b = 1 with rtol =
+// 0, so no kernel turns into a no-op; the handle's solve state is overwritten.
+spmv_status_t cg_timing(spmv_matrix_t A, int iters, double *out, cudaStream_t st) {
+    GB_TRY(ensure_cg_work(A, false, st));
+    CgWork &w = A->cg;
+    CgScalars *sc = outer_scalars(A);
+    double *b = nullptr;
+    GB_CUDA(gb_malloc_async((void **)&b, sizeof(double) * (size_t)A->n, st));
+    fill_value<<<(unsigned)std::min<int64_t>(((int64_t)A->n + 255) / 256, 4096), 256, 0, st>>>(
+        A->n, b, 1.0);
+    cudaEvent_t e[2] = {nullptr, nullptr};
+    spmv_status_t s = cuda_status(cudaEventCreate(&e[0]));
+    if (s == SPMV_OK) s = cuda_status(cudaEventCreate(&e[1]));
+    auto restart = [&]() -> spmv_status_t {
+        set_scalars<<<1, 1, 0, st>>>(sc, 0.0, 1 << 30);
+        GB_LAUNCHED();
+        return enqueue_residual64(A, b, true, true, st);
+    };
+    auto elapsed = [&](float *ms) -> spmv_status_t {
+        GB_CUDA(cudaEventSynchronize(e[1]));
+        GB_CUDA(cudaEventElapsedTime(ms, e[0], e[1]));
+        return SPMV_OK;
+    };
+    const int G = cg_grid(A->n);
+    float ms = 0.f;
+    cudaGraphExec_t g = nullptr;
+    if (s == SPMV_OK) s = get_graph(A, false, iters, &g);
+    if (s == SPMV_OK) s = restart();
+    if (s == SPMV_OK) s = cuda_status(cudaGraphLaunch(g, st));  // warm-up
+    if (s == SPMV_OK) s = cuda_status(cudaEventRecord(e[0], st));
+    if (s == SPMV_OK) s = cuda_status(cudaGraphLaunch(g, st));
+    if (s == SPMV_OK) s = cuda_status(cudaEventRecord(e[1], st));
+    if (s == SPMV_OK) s = elapsed(&ms);
+    out[0] = ms / iters;
+    if (s == SPMV_OK) s = cuda_status(cudaEventRecord(e[0], st));
+    if (s == SPMV_OK) s = enqueue_cg64(A, iters, st);
+    if (s == SPMV_OK) s = cuda_status(cudaEventRecord(e[1], st));
+    if (s == SPMV_OK) s = elapsed(&ms);
+    out[1] = ms / iters;
+    double sum[3] = {0.0, 0.0, 0.0};
+    for (int it = 0; it < iters && s == SPMV_OK; ++it) {
+        for (int k = 0; k < 3 && s == SPMV_OK; ++k) {
+            s = cuda_status(cudaEventRecord(e[0], st));
+            if (s != SPMV_OK) break;
+            if (k == 0) s = enqueue_pq64(A, sc, st);
+            else if (k == 1)
+                cg_update_xr<double><<<G, kCgBlock, 0, st>>>(A->n, w.x.p, w.r.p, w.p.p, w.q.p,
+                                                             w.dinv.p, w.part.p + w.pq_len, sc);
+            else
+                cg_update_p<double><<<G, kCgBlock, 0, st>>>(A->n, w.r.p, w.dinv.p, w.p.p, sc);
+            if (s == SPMV_OK) s = cuda_status(cudaGetLastError());
+            if (s == SPMV_OK) s = cuda_status(cudaEventRecord(e[1], st));
+            if (s == SPMV_OK) s = elapsed(&ms);
+            sum[k] += ms;
+        }
+    }
+    for (int k = 0; k < 3; ++k) out[2 + k] = sum[k] / iters;
+    if (s == SPMV_OK) {
+        const auto t0 = Clock::now();
+        for (int i = 0; i < iters && s == SPMV_OK; ++i) s = read_scalars(A, st, nullptr, nullptr);
+        out[5] = seconds_since(t0) * 1e3 / iters;
+    }
+    if (e[0]) cudaEventDestroy(e[0]);
+    if (e[1]) cudaEventDestroy(e[1]);
+    cudaFreeAsync(b, st);
+    return s;
+}
+
 }  // namespace gb
 
 using namespace gb;
 
 extern "C" {
+
+spmv_status_t spmv_diag_cg_timing(spmv_matrix_t A, int iters, double *ms_out, void *stream) {
+    if (!A || !ms_out || iters < 1 || iters > 4096 || A->n == 0 || A->n != A->n_cols)
+        return SPMV_ERR_INVALID_ARG;
+    if (!A->has64()) return SPMV_ERR_UNSUPPORTED;
+    cudaStream_t st = (cudaStream_t)stream;
+    AllocStream alloc_scope(st);
+    return cg_timing(A, iters, ms_out, st);
+}
 
 spmv_status_t cg_default_options(cg_options_t *o) {
     if (!o) return SPMV_ERR_INVALID_ARG;

@@ -70,6 +70,7 @@ size_t estimate_bytes(int32_t n, int64_t nnz, bool mixed) {
 
 struct spmv_server_s {
     size_t budget = 0;
+    std::atomic<size_t> priority_bytes{0};  // requests at least this large run at high priority
     cudaMemPool_t pool = nullptr;  // stream-ordered allocations of the slots
     int max_slots = 1;
     int device = 0;
@@ -161,10 +162,18 @@ void run_request(Request *r, cudaStream_t st) {
 void worker(spmv_server_t S) {
     cudaSetDevice(S->device);
     AllocPool pool_scope(S->pool);
-    cudaStream_t st = nullptr;
+    // two streams per slot: the default priority, and the device's highest for the requests
+    // the priority threshold names
+    cudaStream_t st = nullptr, st_hi = nullptr;
+    int least = 0, greatest = 0;
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
         st = nullptr;
+    }
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&st_hi, cudaStreamNonBlocking, greatest) != cudaSuccess) {
+        cudaGetLastError();
+        st_hi = nullptr;
     }
     for (;;) {
         Request *r = nullptr;
@@ -181,7 +190,9 @@ void worker(spmv_server_t S) {
             S->active += 1;
         }
         r->t_start = Clock::now();
-        if (st) run_request(r, st);
+        const size_t pb = S->priority_bytes.load(std::memory_order_relaxed);
+        cudaStream_t use = (pb > 0 && r->est_bytes >= pb && st_hi) ? st_hi : st;
+        if (use) run_request(r, use);
         else r->status = SPMV_ERR_CUDA;
         r->t_done = Clock::now();
         {
@@ -204,6 +215,7 @@ void worker(spmv_server_t S) {
         S->cv.notify_all();
     }
     if (st) cudaStreamDestroy(st);
+    if (st_hi) cudaStreamDestroy(st_hi);
 }
 
 double percentile(std::vector<double> v, double q) {
@@ -322,6 +334,12 @@ spmv_status_t spmv_server_poll(spmv_server_t S, uint64_t ticket, double *x_host,
     const spmv_status_t s = r->status;
     delete r;
     return s;
+}
+
+spmv_status_t spmv_server_set_priority_bytes(spmv_server_t S, size_t bytes) {
+    if (!S) return SPMV_ERR_INVALID_ARG;
+    S->priority_bytes.store(bytes, std::memory_order_relaxed);
+    return SPMV_OK;
 }
 
 spmv_status_t spmv_server_get_stats(spmv_server_t S, spmv_server_stats_t *st) {

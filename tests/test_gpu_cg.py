@@ -230,3 +230,13 @@ def test_barrier_wait_runs_out_with_a_status():
     A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values)
     _, res = solve(A, b, rtol=1e-10)
     assert res["status"] == capi.SPMV_OK
+
+
+def test_cg_timing_diagnostic():
+    """spmv_diag_cg_timing reports positive, finite times; the handle still solves afterwards."""
+    m, b = workloads.kuhn(10, seed=2, dirichlet=True)
+    A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values)
+    t = capi.spmv_diag_cg_timing(A.handle, 8)
+    assert all(np.isfinite(v) and v > 0 for v in t.values()), t
+    _, res = solve(A, b, rtol=1e-10)
+    assert res["status"] == capi.SPMV_OK
