@@ -545,7 +545,8 @@ def summary_of(line):
                           "one_at_a_time_plain_fp64": [r3(sv["one_at_a_time_plain_fp64"][f])
                                                        for f in ("solves_per_s", "p50_latency_s",
                                                                  "p99_latency_s")]}
-        for key in ("arrival_0.5x", "arrival_1x", "arrival_2x", "saturated"):
+        for key in ("arrival_0.5x", "arrival_1x", "arrival_1x_priority", "arrival_2x",
+                    "saturated"):
             out["serving"][key] = [r3(sv[key][f]) for f in ("solves_per_s", "p50_latency_s",
                                                             "p99_latency_s")]
         out["serving"]["fields"] = "solves/s, p50 s, p99 s"
@@ -887,9 +888,13 @@ def chain_results(args, torch, capi, flush, stream, dev):
                      precision=capi.SPMV_PREC_DUAL)
     forms = {"fused": capi.SPMV_CHAIN_FUSED, "two_products": capi.SPMV_CHAIN_TWO,
              "tuned": capi.SPMV_CHAIN_AUTO}
+    # the tuned handle keeps the sliced product variant (its slice height and CTA size are
+    # tuned with the chain form): the tuner times a product of x from DRAM, while the chain's
+    # second product reads t = G x from L2
     Mh = {name: capi.Matrix(M.n, M.row_ptr, M.col_idx, M.values, stream=stream,
                             n_cols=M.n_cols, precision=capi.SPMV_PREC_DUAL, chain_form=f,
-                            autotune=int(f == capi.SPMV_CHAIN_AUTO))
+                            autotune=int(f == capi.SPMV_CHAIN_AUTO),
+                            variant=capi.SPMV_VARIANT_SELL)
           for name, f in forms.items()}
     xd = torch.from_numpy(x).to(dev)
     t = torch.empty(G.n, dtype=torch.float64, device=dev)
@@ -1029,11 +1034,16 @@ def serving_results(args, capi, torch):
 
     # (b) served
     served = {}
-    for mult in (0.5, 1.0, 2.0, None):
+    # the largest requests (estimated footprint >= 256 MB: about 1M cells and up) on
+    # high-priority streams, at 1x, beside the same arrivals at the default priority
+    prio_bytes = 256 << 20
+    for mult, prio in ((0.5, 0), (1.0, 0), (1.0, prio_bytes), (2.0, 0), (None, 0)):
         lam = mult * rate_plain if mult else None
         gaps = (np.random.default_rng(2).exponential(1.0 / lam, size=n_req) if mult
                 else np.zeros(n_req))
         srv = capi.spmv_server_create(60 << 30, args.serve_slots)
+        if prio:
+            capi.spmv_server_set_priority_bytes(srv, prio)
         st = stream()
         pending = {}
         results = []
@@ -1071,7 +1081,7 @@ def serving_results(args, capi, torch):
         capi.spmv_server_destroy(srv)
         gen_wait = st.wait_s
         st.close()
-        served["arrival_%gx" % mult if mult else "saturated"] = {
+        served[("arrival_%gx" % mult if mult else "saturated") + ("_priority" if prio else "")] = {
             "arrival_rate_per_s": lam, "offered_rate_per_s": n_req / t_sub,
             "solves_per_s": n_req / t_served,
             "p50_latency_s": s["p50_latency_s"], "p99_latency_s": s["p99_latency_s"],

@@ -7,10 +7,10 @@
 // next (admission waits for it), so none starves.  Its solve then runs on the slot's own CUDA
 // stream, so the kernels of all admitted solves overlap on the GPU while new requests keep
 // arriving.  A slot takes the next request the moment its solve finishes (no batch
-// boundaries).  Each solve
-// keeps its matrix, vectors and CG state in HBM until it completes; only x returns to the
-// host.  Every per-problem kernel uses the same fixed grid and reduction order whatever else
-// runs, so a result is bit-identical alone and in a mix.
+// boundaries).  Each solve keeps its matrix, vectors and CG state in HBM until it completes;
+// only x returns to the host.  Every per-problem kernel uses the same fixed grid and reduction
+// order whatever else runs, so a result is bit-identical alone and in a mix.  Optionally the
+// largest requests run on high-priority streams (spmv_server_set_priority_bytes).
 #include <algorithm>
 #include <atomic>
 #include <chrono>

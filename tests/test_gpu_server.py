@@ -255,3 +255,23 @@ def test_small_request_passes_a_blocked_large_one(oracle):
     assert r1["status"] == capi.SPMV_ERR_CANCELLED
     assert r2["status"] == capi.SPMV_OK and relres(oracle, mb, x2, bb) <= 1e-8
     capi.spmv_server_destroy(srv)
+
+
+def test_priority_streams_leave_results_unchanged(oracle):
+    """Requests above the priority threshold run on high-priority streams; their results are
+    the same bits as at the default priority."""
+    reqs = requests([3e4, 1.2e4, 5e4], seed0=400)
+    o = capi.cg_default_options(rtol=1e-8)
+    outs = []
+    for threshold in (0, 1, 20 << 20):
+        srv = capi.spmv_server_create(8 << 30, 3)
+        capi.spmv_server_set_priority_bytes(srv, threshold)
+        ts = [capi.spmv_server_submit(srv, m.n, m.row_ptr, m.col_idx, m.values, b, o)
+              for m, b in reqs]
+        outs.append(wait_all(srv, ts, [m for m, _ in reqs]))
+        capi.spmv_server_destroy(srv)
+    for i, (m, b) in enumerate(reqs):
+        x0, r0 = outs[0][i]
+        assert r0["status"] == capi.SPMV_OK and relres(oracle, m, x0, b) <= 1e-8
+        for out in outs[1:]:
+            assert np.array_equal(out[i][0], x0)
