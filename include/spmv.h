@@ -93,7 +93,8 @@ typedef struct {
                           * 0 = off (default).  Costs one pass over the matrix at creation. */
     int spmm_form;       /* kernel form of the multi-vector products whose rows are gathered
                           * in 32-byte pieces (SPMV_SPMM_*): AUTO = tuned when autotune is on,
-                          * else the measured default.  Every form gives the same bits. */
+                          * else the measured default (UNROLLED).  Every form gives the same
+                          * bits. */
     int pq_ctas;         /* CG product grid: CTAs per SM (0 = tuned when autotune is on, else
                           * 4; 2..4 explicit).  The grid fixes the reduction order of p.q. */
     int pq_unroll;       /* CG product entries in flight per lane: 0 = tuned / automatic, 2, 5 */
@@ -118,6 +119,9 @@ typedef struct {
 #define SPMV_SPMM_WIDE_GS4 3  /* grid-stride over row blocks, 4 CTAs per SM, the next block's
                                * matrix data prefetched into L2                              */
 #define SPMV_SPMM_WIDE_GS6 4  /* the same at 6 CTAs per SM                                   */
+#define SPMV_SPMM_UNROLLED 5  /* one warp per group of rows, the body unrolled for the slice's
+                               * width (up to 10), the row's matrix loads all in flight; the
+                               * default when not tuned                                      */
 
 /* Invariants verified by spmv_verify, one bit each in its result:                      */
 #define SPMV_CHECK_SLICE_PTR 1  /* slice pointers start at 0, grow by multiples of S, end at

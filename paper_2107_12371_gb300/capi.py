@@ -34,6 +34,7 @@ SPMV_VARIANT_AUTO, SPMV_VARIANT_CSR, SPMV_VARIANT_SELL, SPMV_VARIANT_SELL_WINDOW
 SPMV_VARIANT_SELL_BULK = 4
 SPMV_SPMM_AUTO, SPMV_SPMM_WIDE, SPMV_SPMM_WIDE_PIPE, SPMV_SPMM_WIDE_GS4, SPMV_SPMM_WIDE_GS6 = \
     0, 1, 2, 3, 4
+SPMV_SPMM_UNROLLED = 5
 SPMV_CHAIN_AUTO, SPMV_CHAIN_FUSED, SPMV_CHAIN_TWO = 0, 1, 2
 
 

@@ -59,7 +59,7 @@ static spmv_status_t normalize_options(const spmv_options_t *in, spmv_options_t 
     if (o->sigma != 0 && (o->sigma < 32 || o->sigma > 4096 || (o->sigma & (o->sigma - 1)) != 0))
         return SPMV_ERR_INVALID_ARG;
     if (o->checks != 0 && o->checks != 1) return SPMV_ERR_INVALID_ARG;
-    if (o->spmm_form < SPMV_SPMM_AUTO || o->spmm_form > SPMV_SPMM_WIDE_GS6)
+    if (o->spmm_form < SPMV_SPMM_AUTO || o->spmm_form > SPMV_SPMM_UNROLLED)
         return SPMV_ERR_INVALID_ARG;
     if (o->pq_ctas != 0 && (o->pq_ctas < 2 || o->pq_ctas > 4)) return SPMV_ERR_INVALID_ARG;
     if (o->pq_unroll != 0 && o->pq_unroll != 2 && o->pq_unroll != 5) return SPMV_ERR_INVALID_ARG;

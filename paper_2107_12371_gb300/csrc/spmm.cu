@@ -479,16 +479,154 @@ spmm_sell_wide_gs(int32_t n, int32_t S, int32_t n_slices, const int64_t *__restr
     }
 }
 
+// The rows of one warp of the 256-bit SpMM with the slice width W known at compile time: the W
+// (value, column) pairs of the lane's row are requested together, then the X rows gathered two
+// at a time and multiplied in entry order.  With a runtime width the compiler keeps each pair's
+// matrix loads behind the previous pair's gathers; unrolled, the matrix loads of the whole row
+// are in flight at once and a row costs one dependent matrix round instead of one per pair.
+template <typename T, int G, int W, typename ColT>
+__device__ __forceinline__ void wide_row_w(int64_t at, int32_t S, ColT cols, int32_t cb,
+                                           const T *__restrict__ val, const T *__restrict__ xg,
+                                           uint64_t pol, T (&acc)[Wide<T>::n]) {
+    constexpr int VW = Wide<T>::n;
+    constexpr int K = VW * G;
+    T a[W];
+    int32_t c[W];
+#pragma unroll
+    for (int t = 0; t < W; ++t) {
+        T a1[1];
+        int32_t c1[1];
+        ld_stream(val + at + (int64_t)t * S, pol, a1);
+        cols.template load<1>(at + (int64_t)t * S, 0, pol, cb, c1);
+        a[t] = a1[0];
+        c[t] = c1[0];
+    }
+#pragma unroll
+    for (int t = 0; t < W; t += 2) {
+        T xv[2][VW];
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+            if (t + u < W && c[t + u] >= 0) Wide<T>::load(xg + (int64_t)c[t + u] * K, xv[u]);
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+            if (t + u < W && c[t + u] >= 0) {
+#pragma unroll
+                for (int j = 0; j < VW; ++j) acc[j] = fma_t(a[t + u], xv[u][j], acc[j]);
+            }
+    }
+}
+
+// The 256-bit SpMM with each slice's width dispatched to a fully unrolled row body for widths
+// up to WMAX (wider slices: the two-entries-per-step loop of spmm_sell_wide), MINB CTAs per SM.
+// Measured on the 87^3 mixed mesh (us, k = 8 / 32): FP32 59 / 170 against 64 / 207 for the best
+// earlier form, FP64 174 / 651 against 178 / 664, at six CTAs per SM and WMAX = 10.  Same
+// entry order and fused multiply-add from +0.0 as the other SpMM kernels, so the results are
+// identical.
+template <typename T, int G, int MINB, int WMAX, typename ColT>
+__global__ void __launch_bounds__(256, MINB)
+spmm_sell_unrolled(int32_t n, int32_t S, int32_t n_slices, const int64_t *__restrict__ sp,
+                   ColT cols, const T *__restrict__ val, const T *__restrict__ X,
+                   T *__restrict__ Y) {
+    constexpr int VW = Wide<T>::n;
+    constexpr int K = VW * G;
+    constexpr int RPW = 32 / G;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane / G, g = lane % G;
+    const int64_t rows_total = (int64_t)n_slices * S;
+    const int64_t row0 = gw * RPW;
+    if (row0 >= rows_total) return;  // whole warp: rows_total is a multiple of RPW
+    const int64_t row = row0 + sub;
+    const int64_t slice = row0 / S;
+    const int64_t base = sp[slice];
+    const int w = (int)((sp[slice + 1] - base) / S);
+    const int32_t cb = cols.base(slice);
+    const uint64_t pol = policy_evict_first();
+    const int64_t at = base + (row - slice * S);
+    const T *xg = X + g * VW;
+    T acc[VW];
+#pragma unroll
+    for (int j = 0; j < VW; ++j) acc[j] = T(0);
+    switch (w) {
+        case 0: break;
+        case 1: wide_row_w<T, G, 1>(at, S, cols, cb, val, xg, pol, acc); break;
+        case 2: wide_row_w<T, G, 2>(at, S, cols, cb, val, xg, pol, acc); break;
+        case 3: wide_row_w<T, G, 3>(at, S, cols, cb, val, xg, pol, acc); break;
+        case 4: wide_row_w<T, G, 4>(at, S, cols, cb, val, xg, pol, acc); break;
+        case 5: wide_row_w<T, G, 5>(at, S, cols, cb, val, xg, pol, acc); break;
+        case 6: wide_row_w<T, G, 6>(at, S, cols, cb, val, xg, pol, acc); break;
+        case 7:
+            if constexpr (WMAX >= 7) {
+                wide_row_w<T, G, 7>(at, S, cols, cb, val, xg, pol, acc);
+                break;
+            }
+            [[fallthrough]];
+        case 8:
+            if constexpr (WMAX >= 8) {
+                wide_row_w<T, G, 8>(at, S, cols, cb, val, xg, pol, acc);
+                break;
+            }
+            [[fallthrough]];
+        case 9:
+            if constexpr (WMAX >= 9) {
+                wide_row_w<T, G, 9>(at, S, cols, cb, val, xg, pol, acc);
+                break;
+            }
+            [[fallthrough]];
+        case 10:
+            if constexpr (WMAX >= 10) {
+                wide_row_w<T, G, 10>(at, S, cols, cb, val, xg, pol, acc);
+                break;
+            }
+            [[fallthrough]];
+        default: {
+            int t = 0;
+            for (; t + 2 <= w; t += 2) {
+                T a[2][1];
+                int32_t c[2][1];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    ld_stream(val + at + (int64_t)(t + u) * S, pol, a[u]);
+                    cols.template load<1>(at + (int64_t)(t + u) * S, 0, pol, cb, c[u]);
+                }
+                T xv[2][VW];
+#pragma unroll
+                for (int u = 0; u < 2; ++u)
+                    if (c[u][0] >= 0) Wide<T>::load(xg + (int64_t)c[u][0] * K, xv[u]);
+#pragma unroll
+                for (int u = 0; u < 2; ++u)
+                    if (c[u][0] >= 0) {
+#pragma unroll
+                        for (int j = 0; j < VW; ++j) acc[j] = fma_t(a[u][0], xv[u][j], acc[j]);
+                    }
+            }
+            if (t < w) {
+                T a[1];
+                int32_t c[1];
+                ld_stream(val + at + (int64_t)t * S, pol, a);
+                cols.template load<1>(at + (int64_t)t * S, 0, pol, cb, c);
+                if (c[0] >= 0) {
+                    T xv[VW];
+                    Wide<T>::load(xg + (int64_t)c[0] * K, xv);
+#pragma unroll
+                    for (int j = 0; j < VW; ++j) acc[j] = fma_t(a[0], xv[j], acc[j]);
+                }
+            }
+        }
+    }
+    if (row < n) Wide<T>::store(Y + row * K + g * VW, acc);
+}
+
 }  // namespace
 
 // Kernel form of the 256-bit SpMM for a handle, precision and lanes-per-row class: the
-// handle's choice (option or tuner), else the measured default (the software-pipelined form
-// for FP32 rows of one lane, the plain form otherwise).
+// handle's choice (option or tuner), else the measured default, the width-unrolled form
+// (fastest of the forms for k = 8 and 32 in both precisions on the mixed-element mesh).
 int spmm_form_of(const spmv_matrix_t A, bool f32, int gi) {
     if (A->opt.spmm_form != SPMV_SPMM_AUTO) return A->opt.spmm_form;
     const int t = A->spmm_tuned[f32 ? 1 : 0][gi];
     if (t != SPMV_SPMM_AUTO) return t;
-    return (f32 && gi == 0) ? SPMV_SPMM_WIDE_PIPE : SPMV_SPMM_WIDE;
+    return SPMV_SPMM_UNROLLED;
 }
 
 namespace {
@@ -522,6 +660,10 @@ spmv_status_t launch_spmm(spmv_matrix_t A, int k, const T *val, const T *X, T *Y
                     break;
                 case SPMV_SPMM_WIDE_GS6:
                     spmm_sell_wide_gs<T, G, 6, ColT><<<sms * 6, block, 0, st>>>(
+                        A->n, A->S, A->n_slices, A->slice_ptr.p, cols, val, X, Y);
+                    break;
+                case SPMV_SPMM_UNROLLED:
+                    spmm_sell_unrolled<T, G, 6, 10, ColT><<<grid, block, 0, st>>>(
                         A->n, A->S, A->n_slices, A->slice_ptr.p, cols, val, X, Y);
                     break;
                 default:
@@ -619,7 +761,7 @@ spmv_status_t tune_spmm(spmv_matrix_t A, int k, const T *val, const T *X, T *Y,
     if (s == SPMV_OK) s = cuda_status(cudaEventCreate(&e1));
     float best = 1e30f;
     int best_form = SPMV_SPMM_WIDE;
-    for (int form = SPMV_SPMM_WIDE; form <= SPMV_SPMM_WIDE_GS6 && s == SPMV_OK; ++form) {
+    for (int form = SPMV_SPMM_WIDE; form <= SPMV_SPMM_UNROLLED && s == SPMV_OK; ++form) {
         slot = form;
         s = launch_spmm<T>(A, k, val, X, Y, st);
         float t[3];

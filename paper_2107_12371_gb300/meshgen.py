@@ -34,6 +34,7 @@ seed gives the same bits on any platform.
 from __future__ import annotations
 
 import os
+import threading
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -398,20 +399,24 @@ def kuhn_tet_matrix(n, ny=None, nz=None, *, jitter=0.2, seed=0, dirichlet=False,
 
 _FAST_SRC = os.path.join(os.path.dirname(os.path.abspath(__file__)), "kuhnbox.c")
 _fast_lib = None
+_fast_lock = threading.Lock()
 
 
 def build_fast(force: bool = False) -> str:
-    """Compile kuhnbox.c (the closed-form Kuhn-box assembler) into lib/libgb300_kuhnbox.so."""
+    """Compile kuhnbox.c (the closed-form Kuhn-box assembler) into lib/libgb300_kuhnbox.so.
+    Safe to call from several threads (the generator threads of the serving stream)."""
     import subprocess
     out_dir = os.path.join(os.path.dirname(_FAST_SRC), "lib")
     os.makedirs(out_dir, exist_ok=True)
     path = os.path.join(out_dir, "libgb300_kuhnbox.so")
-    if not force and os.path.exists(path) and os.path.getmtime(path) >= os.path.getmtime(_FAST_SRC):
-        return path
-    tmp = path + ".tmp%d" % os.getpid()
-    subprocess.check_call([os.environ.get("CC", "gcc"), "-O3", "-ffp-contract=off", "-fPIC",
-                           "-shared", "-std=c11", "-o", tmp, _FAST_SRC, "-lm"])
-    os.replace(tmp, path)
+    with _fast_lock:
+        if (not force and os.path.exists(path)
+                and os.path.getmtime(path) >= os.path.getmtime(_FAST_SRC)):
+            return path
+        tmp = path + ".tmp%d.%d" % (os.getpid(), threading.get_ident())
+        subprocess.check_call([os.environ.get("CC", "gcc"), "-O3", "-ffp-contract=off", "-fPIC",
+                               "-shared", "-std=c11", "-o", tmp, _FAST_SRC, "-lm"])
+        os.replace(tmp, path)
     return path
 
 

@@ -16,7 +16,7 @@ from paper_2107_12371_gb300 import capi, meshgen, workloads
 pytestmark = pytest.mark.gpu
 
 FORMS = [capi.SPMV_SPMM_WIDE, capi.SPMV_SPMM_WIDE_PIPE, capi.SPMV_SPMM_WIDE_GS4,
-         capi.SPMV_SPMM_WIDE_GS6]
+         capi.SPMV_SPMM_WIDE_GS6, capi.SPMV_SPMM_UNROLLED]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -57,6 +57,28 @@ def test_every_spmm_form_is_bit_exact(oracle, form, bits, S, reorder):
             assert np.array_equal(_spmm(A, X), ref), (dtype, k)
     info = A.info()
     assert info["spmm_form"] == [[form] * 4, [form] * 4]
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_every_spmm_form_on_every_slice_width(oracle, form):
+    """Slices of every width from 0 (all rows empty) to 13: slice s of 64 rows holds rows of s
+    entries (distinct seeded columns), no reordering and no sorting, so the width-unrolled form
+    runs each of its unrolled bodies (1..10), its empty case and its loop for 11..13; a ragged
+    last slice of 20 rows.  k = 8 and 32, FP64 and FP32."""
+    rng = np.random.default_rng(7)
+    widths = [s for s in range(14) for _ in range(64)] + [5] * 20
+    n = len(widths)
+    rp = np.zeros(n + 1, np.int64)
+    rp[1:] = np.cumsum(widths)
+    ci = np.concatenate([np.sort(rng.choice(n, w, replace=False)) for w in widths]).astype(np.int32)
+    v = rng.uniform(-1, 1, ci.size)
+    A = capi.Matrix(n, rp, ci, v, reorder=capi.SPMV_REORDER_NONE, precision=capi.SPMV_PREC_DUAL,
+                    slice_height=64, spmm_form=form)
+    for dtype in (np.float64, np.float32):
+        for k in (8, 32):
+            X = rng.uniform(-1, 1, (n, k)).astype(dtype)
+            ref = oracle.spmm(rp, ci, v.astype(dtype), X, use_fma=True)
+            assert np.array_equal(_spmm(A, X), ref), (dtype, k)
 
 
 def test_tuned_spmm_reports_its_pick_and_is_bit_exact(oracle):
