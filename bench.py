@@ -278,7 +278,7 @@ def run_profile_kernel(args):
         k, dt = int(what.split("_")[1][1:]), what.split("_")[2]
         m, X = workloads.mixed(87, seed=1, k=32)
         A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values, reorder=capi.SPMV_REORDER_RCM,
-                        precision=capi.SPMV_PREC_DUAL, sigma=1024)
+                        precision=capi.SPMV_PREC_DUAL, sigma=1024, spmm_form=args.spmm_form)
         Xd = torch.from_numpy(np.ascontiguousarray(X[:, :k])).to(
             dev, torch.float64 if dt == "f64" else torch.float32)
         Yd = torch.empty_like(Xd)
@@ -1144,6 +1144,8 @@ def main():
                     help="with --profile: time the FP32 product of the handle instead")
     ap.add_argument("--profile-kernel", default="",
                     help="spmm_k8_f64 | spmm_k32_f32 | ... | chain: launch only that kernel")
+    ap.add_argument("--spmm-form", type=int, default=0,
+                    help="with --profile-kernel spmm_*: the SPMV_SPMM_* form (0 = default)")
     ap.add_argument("--profile-cg", type=int, default=0,
                     help="with --profile: also run CG solves capped at this many iterations")
     ap.add_argument("--serve-requests", type=int, default=2000)
