@@ -490,6 +490,7 @@ def run_gpu(args):
     }
     if traffic:
         line["roofline"]["dram_bytes_frac"] = traffic / avg_launch_s / 1e9 / peak
+        line["roofline"]["dram_bytes_per_nnz"] = traffic / nnz
         line["roofline"]["dram_bytes_note"] = (
             "DRAM bytes an ncu capture counted per launch (16-bit columns move fewer bytes than "
             "the algorithmic 12 B per non-zero) / launch time / copy peak")
