@@ -423,15 +423,15 @@ def run_gpu(args):
     e2e_serial_s = ev0.elapsed_time(ev1) / 1e3 / e2e_steps
 
     # through spmv_apply_host_async: one C-ABI call per step with x and y in pinned host
-    # memory, steps alternating between two streams (and two host buffer pairs), so that
+    # memory, steps taking three streams (and three host buffer pairs) in turn, so that
     # consecutive calls overlap (wall clock, host timer between full synchronisations)
-    streams = [stream, torch.cuda.Stream(device=dev)]
-    xhs = [xh, xh.clone().pin_memory()]
-    yhs = [yh, torch.empty(n, dtype=torch.float64).pin_memory()]
+    streams = [stream] + [torch.cuda.Stream(device=dev) for _ in range(2)]
+    xhs = [xh] + [xh.clone().pin_memory() for _ in range(2)]
+    yhs = [yh] + [torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(2)]
 
     def host_steps(steps):
         for j in range(steps):
-            A.apply_host_async(xhs[j & 1], yhs[j & 1], streams[j & 1])
+            A.apply_host_async(xhs[j % 3], yhs[j % 3], streams[j % 3])
 
     host_steps(4)
     torch.cuda.synchronize(dev)
@@ -470,9 +470,9 @@ def run_gpu(args):
         "clocks": clocks,
         "e2e": {"value": nbytes / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": 8 * n,
                 "d2h_bytes_per_step": 8 * n,
-                "call": "spmv_apply_host_async, steps alternating between two streams "
-                        "(pinned host x and y; the copies of one call overlap the product and "
-                        "copies of the other)",
+                "call": "spmv_apply_host_async, steps taking three streams in turn (pinned "
+                        "host x and y; the copies of one call overlap the products and "
+                        "copies of the others)",
                 "one_call_at_a_time_value": nbytes / e2e_single_s / 1e9,
                 "one_call_at_a_time": "spmv_apply_host (synchronous; copy of x, product and "
                                       "copy of y overlapped by eight runs of slices)",

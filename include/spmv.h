@@ -228,9 +228,10 @@ spmv_status_t spmv_apply_host(spmv_matrix_t A, const double *x_host, double *y_h
  * spmv_apply_host_async -- async.  The same product, enqueued without waiting: `stream` reaches
  * the end of the call's work once y_host holds the result; until then the caller must not
  * change x_host or read y_host.  x, the product and y move in one piece each (no runs);
- * successive calls use two device staging sets in turn, so two calls issued on different
- * streams overlap (the copies of one with the product of the other); a staging set is reused
- * only after its previous call is done with it.
+ * successive calls use three device staging sets in turn (3 x (n_cols + n_rows) doubles,
+ * allocated on the first host call and counted in device_bytes), so calls issued on different
+ * streams overlap (the copy of one call's x with an earlier call's y and with the products); a
+ * staging set is reused only after its previous call is done with it.
  */
 spmv_status_t spmv_apply_host_async(spmv_matrix_t A, const double *x_host, double *y_host,
                                     void *stream);

@@ -189,15 +189,16 @@ struct spmv_matrix_s {
     gb::DevBuf<double> chain_t;
     gb::DevBuf<float> chain_t32;
 
-    // spmv_apply_host(_async): two staging sets used in turn, each with device copies of x and
-    // y, two streams of its own (product, device-to-host) and events; created on first use
+    // spmv_apply_host(_async): three staging sets used in turn, each with device copies of x
+    // and y, two streams of its own (product, device-to-host) and events; created on first use
     static constexpr int kHostChunks = 8;
+    static constexpr int kHostStages = 3;
     struct HostStage {
         gb::DevBuf<double> x, y;
         cudaStream_t sk = nullptr, sy = nullptr;
         cudaEvent_t ev_x[kHostChunks] = {}, ev_k[kHostChunks] = {};
         cudaEvent_t x_free = nullptr, y_free = nullptr;  // end of the last use's reads of x, y
-    } h_stage[2];
+    } h_stage[kHostStages];
     int h_next = 0;                         // staging set of the next call
     int h_chunks = 0;                       // 0 = not prepared
     int32_t h_slice[kHostChunks + 1] = {};  // chunk c = slices [h_slice[c], h_slice[c + 1])

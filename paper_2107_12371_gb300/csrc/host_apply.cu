@@ -7,10 +7,14 @@
 // rows of y go back to the host on a third stream while later runs compute: the three
 // transfers of the paper's task (x in, product, y out) are pipelined instead of serialised.
 // The asynchronous form moves x, the product and y in one piece each instead (runs of slices
-// cost copy efficiency when calls already overlap each other); its calls alternate between
-// two staging sets, so two calls on different streams overlap (the copies of one with the
-// product of the other); a set is reused only after its previous call has finished with it.  Each run is the ordinary product kernel on a view of the
-// handle restricted to its slices, so y is bit-identical to spmv_apply's.
+// cost copy efficiency when calls already overlap each other); its calls take three staging
+// sets in turn, so calls on different streams overlap (the copy of one call's x with the copy
+// of an earlier call's y and with products); a set is reused only after its previous call has
+// finished with it.  With two sets the copy of x for call i + 2 had to wait for call i's y,
+// which starts a product later than the copy of x for call i + 1 ends, leaving the
+// host-to-device link idle for a product's time every step.  Each run is the ordinary
+// product kernel on a view of the handle restricted to its slices, so y is bit-identical to
+// spmv_apply's.
 #include <algorithm>
 #include <vector>
 
@@ -59,7 +63,7 @@ spmv_status_t enqueue_host_apply(spmv_matrix_t A, const double *x_host, double *
                                  cudaStream_t st, bool one_run) {
     GB_TRY(prepare_host_apply(A, st));
     auto &h = A->h_stage[A->h_next];
-    A->h_next ^= 1;
+    A->h_next = (A->h_next + 1) % spmv_matrix_s::kHostStages;
     const int C = one_run ? 1 : A->h_chunks;
     // this set's previous call: its products have read x (x_free) and its copies have read y
     // (y_free); events never recorded yet are no-ops

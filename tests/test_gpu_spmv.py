@@ -584,20 +584,21 @@ def test_apply_host_matches_device(oracle, case):
     assert np.array_equal(y2, y_host)
 
 
-def test_apply_host_async_overlapping_calls(oracle):
-    """Calls enqueued on two streams in turn (three calls, so the first staging set is reused
-    while the second call may still run) each deliver their own product."""
+@pytest.mark.parametrize("n_streams", [1, 2, 3, 4])
+def test_apply_host_async_overlapping_calls(oracle, n_streams):
+    """Seven calls enqueued on 1..4 streams in turn (more calls than the three staging sets,
+    so sets are reused while earlier calls may still run) each deliver their own product."""
     m, _ = workloads.kuhn(12, seed=9, dirichlet=True)
     A = capi.Matrix(m.n, m.row_ptr, m.col_idx, m.values, reorder=capi.SPMV_REORDER_RCM)
     rp, ci, v = capi.spmv_export_csr(A.handle, m.n, m.nnz)
     rng = np.random.default_rng(3)
-    xs = [torch.from_numpy(rng.uniform(-1, 1, m.n)).pin_memory() for _ in range(5)]
-    ys = [torch.full((m.n,), np.nan, dtype=torch.float64).pin_memory() for _ in range(5)]
-    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
-    for j in range(5):
-        A.apply_host_async(xs[j], ys[j], streams[j % 2])
+    xs = [torch.from_numpy(rng.uniform(-1, 1, m.n)).pin_memory() for _ in range(7)]
+    ys = [torch.full((m.n,), np.nan, dtype=torch.float64).pin_memory() for _ in range(7)]
+    streams = [torch.cuda.Stream() for _ in range(n_streams)]
+    for j in range(7):
+        A.apply_host_async(xs[j], ys[j], streams[j % n_streams])
     torch.cuda.synchronize()
-    for j in range(5):
+    for j in range(7):
         ref = oracle.spmv(rp, ci, v, xs[j].numpy(), use_fma=True)
         assert np.array_equal(ys[j].numpy(), ref), j
 
