@@ -495,11 +495,13 @@ def run_gpu(args):
             "DRAM bytes an ncu capture counted per launch (16-bit columns move fewer bytes than "
             "the algorithmic 12 B per non-zero) / launch time / copy peak")
     line.update(extra)
-    if rank == 0 and not args.quick and args.serve_requests > 0:
-        line.update(serving_results(args, capi, torch))
+    # the oracle on the host cores before the serving passes, whose tens of GB of generated
+    # requests leave the host's memory in a state that slowed the threaded oracle several-fold
     if not args.no_cpu_baseline:
         rp, ci, v = capi.spmv_export_csr(A.handle, n, nnz)
         line["cpu_baseline"] = cpu_baseline(rp, ci, v, xi.cpu().numpy(), nbytes)
+    if rank == 0 and not args.quick and args.serve_requests > 0:
+        line.update(serving_results(args, capi, torch))
     line["summary"] = summary_of(line)
     print(json.dumps(line), flush=True)
     if world > 1:
