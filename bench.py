@@ -495,8 +495,8 @@ def run_gpu(args):
             "DRAM bytes an ncu capture counted per launch (16-bit columns move fewer bytes than "
             "the algorithmic 12 B per non-zero) / launch time / copy peak")
     line.update(extra)
-    # the oracle on the host cores before the serving passes, whose tens of GB of generated
-    # requests leave the host's memory in a state that slowed the threaded oracle several-fold
+    # the oracle on the host cores before the serving passes: timed after them (tens of GB of
+    # generated requests allocated and freed) the threaded oracle measured several times slower
     if not args.no_cpu_baseline:
         rp, ci, v = capi.spmv_export_csr(A.handle, n, nnz)
         line["cpu_baseline"] = cpu_baseline(rp, ci, v, xi.cpu().numpy(), nbytes)
